@@ -1,0 +1,253 @@
+/*
+ * lsyn.h — C ABI of the GB300 (sm_103a) library for bottom-up semantic
+ * enumeration of LTLf formulae from positive and negative example traces.
+ *
+ * The method is the one of "GPU accelerated program synthesis: Enumerate
+ * semantics, not syntax!" (arXiv 2504.18943):
+ *
+ *  - A specification (P, N) is a pair of finite sets of finite traces over the
+ *    powerset of the propositions p0..p{n-1}; a formula separates (P, N) when it
+ *    holds at position 0 of every trace of P and of no trace of N (section
+ *    "Synthesising linear temporal logic formulae from examples").
+ *  - Formulae: atoms, not (!), and (&), or (|), next (X), future (F),
+ *    globally (G, read as "not F not"), until (U). Size = number of syntax-tree
+ *    nodes. Satisfaction is over finite traces; nothing holds at or beyond the
+ *    end of a trace.
+ *  - A formula is represented only by its characteristic matrix (CM): one word
+ *    per trace whose bit t says whether the formula holds at position t
+ *    (section "Parallel enumeration of LTLf formulae on GPUs", characteristic
+ *    sequence and matrix). Two formulae with equal CMs are observationally
+ *    equivalent and only the first one found is kept.
+ *  - Level k (all new CMs of size k) is built from levels < k by bitwise
+ *    operators (paragraph "Logical operations as bitwise operations"), every
+ *    candidate is checked against the specification, and new CMs go into a
+ *    device-resident language cache (the listing of paragraph "A generic program
+ *    synthesiser", section "Program synthesis"). The first level that holds a
+ *    separating CM gives a minimal-size formula.
+ *
+ * Conventions for every call:
+ *  - Return value: an lsyn_status. Negative values are errors; no C++
+ *    exception crosses this boundary. lsyn_last_error() gives a message.
+ *  - Pointers documented as "host" point to ordinary CPU memory; the library
+ *    copies what it needs before returning (inputs) or writes results there
+ *    before returning (outputs). The caller keeps ownership.
+ *  - Device memory is owned by the context and released by lsyn_destroy().
+ *  - One context is used by one host thread at a time. All device work of a
+ *    context is issued on the stream given in lsyn_config.
+ *  - Formula text: prefix, fully parenthesised, atoms p0..p{n-1}, e.g.
+ *    "(U (! p1) (& p0 (X p1)))". Unary: "(! f)", "(X f)", "(F f)", "(G f)";
+ *    binary: "(& f g)", "(| f g)", "(U f g)".
+ */
+#ifndef LSYN_H_
+#define LSYN_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LSYN_OK = 0,
+  LSYN_NOT_FOUND = 1,       /* no separating formula up to the requested size */
+  LSYN_PENDING = 2,         /* (serving) the request is not finished yet */
+  LSYN_E_INVAL = -1,        /* an argument is out of range or inconsistent */
+  LSYN_E_NOMEM = -2,        /* a device allocation failed */
+  LSYN_E_CUDA = -3,         /* a CUDA runtime call failed */
+  LSYN_E_UNSUPPORTED = -4,  /* a valid request this build does not handle */
+  LSYN_E_CACHE_FULL = -5,   /* the language cache ran out of space: deeper levels cannot be built */
+  LSYN_E_TIMEOUT = -6,      /* a deadline passed between levels */
+  LSYN_E_STATE = -7         /* call out of order, or an internal consistency check failed */
+} lsyn_status;
+
+/* Operator mask bits (lsyn_config.op_mask). */
+#define LSYN_OP_NOT 0x01u
+#define LSYN_OP_AND 0x02u
+#define LSYN_OP_OR 0x04u
+#define LSYN_OP_X 0x08u
+#define LSYN_OP_F 0x10u
+#define LSYN_OP_G 0x20u
+#define LSYN_OP_U 0x40u
+#define LSYN_OPS_ALL 0x7Fu
+/* The grammar printed in the paper: atoms, not, and, X, F, U. */
+#define LSYN_OPS_PAPER (LSYN_OP_NOT | LSYN_OP_AND | LSYN_OP_X | LSYN_OP_F | LSYN_OP_U)
+
+/*
+ * A specification (P, N), positives first (section "Synthesising linear
+ * temporal logic formulae from examples"; the fixed total order on P ∪ N of the
+ * characteristic matrix, section "Parallel enumeration of LTLf formulae on
+ * GPUs").
+ *   n_props     number of atomic propositions, 1..32.
+ *   n_pos       |P| >= 0;  n_neg = |N| >= 0;  n_pos + n_neg >= 1.
+ *   word_bits   32 or 64: bits per characteristic-sequence word; every trace
+ *               must be at most this long.
+ *   lengths     host, int32[n_pos + n_neg]: trace lengths, each 1..word_bits.
+ *   atom_words  host, [n_props][n_pos + n_neg] words of word_bits bits
+ *               (uint32_t or uint64_t), row-major by proposition. Bit t of word
+ *               (p, i) is 1 iff p holds at position t of trace i. Bits at
+ *               positions >= lengths[i] are ignored.
+ */
+typedef struct {
+  int32_t n_props;
+  int32_t n_pos;
+  int32_t n_neg;
+  int32_t word_bits;
+  const int32_t* lengths;
+  const void* atom_words;
+} lsyn_problem;
+
+/* Device allocator hooks: return a device pointer (NULL on failure) / free it. */
+typedef void* (*lsyn_alloc_fn)(size_t bytes, void* user);
+typedef void (*lsyn_free_fn)(void* ptr, void* user);
+
+/*
+ * Context configuration. A zero-filled struct selects every default.
+ *   op_mask      operators to enumerate (LSYN_OP_*); 0 = LSYN_OPS_ALL.
+ *   cache_bytes  device bytes for the language cache: CM arena, provenance and
+ *                hash table together; 0 = 1 GiB.
+ *   table_load   maximum load factor of the hash table in (0, 0.9]; 0 = 0.5.
+ *   full_levels  0: a level stops at its first separating candidate (the early
+ *                return of the listing); 1: every level is built completely even
+ *                when it holds a solution (used to compare whole levels).
+ *   timing       1 records CUDA events around each kernel launch and fills the
+ *                kernel_ms fields of lsyn_level_stats.
+ *   alloc, free, alloc_user   device allocator (e.g. the PyTorch caching
+ *                allocator); NULL = cudaMalloc / cudaFree.
+ *   stream       cudaStream_t for all device work; NULL = the legacy default stream.
+ *   device       CUDA device ordinal; -1 or 0..n-1 (the current device if -1).
+ */
+typedef struct {
+  uint32_t op_mask;
+  uint64_t cache_bytes;
+  float table_load;
+  int32_t full_levels;
+  int32_t timing;
+  lsyn_alloc_fn alloc;
+  lsyn_free_fn free;
+  void* alloc_user;
+  void* stream;
+  int32_t device;
+} lsyn_config;
+
+/* Per-level statistics (filled by lsyn_enumerate_level). */
+typedef struct {
+  int32_t level;          /* k */
+  int32_t solved;         /* 1 if a candidate of this level separates (P, N) */
+  int32_t cache_full;     /* 1 if an insert failed for lack of space: the level is incomplete */
+  int32_t early_exit;     /* 1 if the level stopped at a solution before building every candidate */
+  int64_t candidates;     /* candidate formulae built at this level (and/or once per unordered pair) */
+  int64_t unique;         /* new characteristic matrices added to the cache: |L_k| */
+  int64_t total;          /* entries in the cache after this level */
+  int64_t deferred;       /* candidates re-examined after meeting an unpublished slot */
+  double ms;              /* wall time of the level (host clock, includes the final sync) */
+  double kernel_ms[4];    /* with timing=1: device time of the unary, binary, resolve and other launches */
+  double bytes_alg;       /* algorithmic bytes of the level (operand reads, probes, compares, inserts) */
+  double bytes_binary;    /* the part of bytes_alg moved by the binary-operator launches */
+  int32_t launches;       /* kernel launches issued for this level */
+  int32_t reserved;
+} lsyn_level_stats;
+
+/*
+ * Result of lsyn_solve.
+ *   formula / formula_cap  caller-owned host buffer for the formula text
+ *                          (LSYN_E_INVAL if too small).
+ *   level_stats / level_stats_cap  optional caller-owned host array: entry
+ *                          k - 1 receives the statistics of level k when this
+ *                          call builds level k and k <= level_stats_cap.
+ */
+typedef struct {
+  int32_t found;          /* 1 if a separating formula was found */
+  int32_t size;           /* its size (syntax-tree nodes) */
+  int32_t exact;          /* 1 if minimal: every smaller level was complete */
+  int32_t levels_done;    /* levels built so far */
+  int64_t constructed;    /* candidates built over all levels, atoms included */
+  int64_t unique;         /* entries in the language cache */
+  double ms;              /* wall time of the call */
+  int32_t launches;       /* kernel launches issued by this call */
+  int32_t level_stats_cap;
+  lsyn_level_stats* level_stats;
+  char* formula;
+  size_t formula_cap;
+} lsyn_result;
+
+typedef struct lsyn_ctx lsyn_ctx;
+
+/*
+ * Create a context for one specification: validates the problem, allocates the
+ * language cache and scratch on the device, copies the traces there and builds
+ * nothing yet. *out receives the context, or NULL on error (then
+ * lsyn_last_error(NULL) explains). Errors: LSYN_E_INVAL (bad sizes, lengths out
+ * of 1..word_bits, more than 2^30 - 2 cache entries requested), LSYN_E_NOMEM,
+ * LSYN_E_CUDA.
+ */
+lsyn_status lsyn_create(const lsyn_problem* problem, const lsyn_config* config, lsyn_ctx** out);
+
+/* Release every device buffer of the context (after its stream's work is done). NULL is allowed. */
+void lsyn_destroy(lsyn_ctx* ctx);
+
+/* Message of the last error on this context; with NULL, of the last failed lsyn_create on this thread. */
+const char* lsyn_last_error(const lsyn_ctx* ctx);
+
+/* Forget every level (keeps the traces and the memory); the next level to build is 1. */
+lsyn_status lsyn_reset(lsyn_ctx* ctx);
+
+/*
+ * Build level k = levels_done + 1 (the listing of "A generic program
+ * synthesiser": every operator, every split of k-1 into child sizes, every
+ * pair of cached programs; level 1 is the distinct atoms). Every candidate is
+ * checked against the specification; new CMs are inserted into the cache.
+ * out (host, may be NULL) receives the level's statistics.
+ * Errors: LSYN_E_STATE if k is not the next level, or the previous level is
+ * incomplete (cache full or stopped early); LSYN_E_CACHE_FULL is NOT returned
+ * here (see out->cache_full); LSYN_E_CUDA.
+ */
+lsyn_status lsyn_enumerate_level(lsyn_ctx* ctx, int32_t k, lsyn_level_stats* out);
+
+/*
+ * Build levels until one holds a separating formula, or max_size (1..64) is
+ * passed. On LSYN_OK out->formula holds a separating formula of minimal size
+ * out->size (minimal when out->exact is 1). Returns LSYN_NOT_FOUND when no
+ * formula up to max_size separates, LSYN_E_CACHE_FULL when the cache filled up
+ * before a solution was found (levels up to out->levels_done are exact).
+ */
+lsyn_status lsyn_solve(lsyn_ctx* ctx, int32_t max_size, lsyn_result* out);
+
+/* Number of entries of level k (1 <= k <= levels_done) in *n_out. */
+lsyn_status lsyn_level_count(const lsyn_ctx* ctx, int32_t k, int64_t* n_out);
+
+/*
+ * Copy the CMs of entries [first, first + count) of level k into dst (host):
+ * count rows of (n_pos + n_neg) words of word_bits bits, positives first, the
+ * rows in the cache's (unspecified, run-dependent) order. cap = bytes of dst.
+ */
+lsyn_status lsyn_export_level(lsyn_ctx* ctx, int32_t k, int64_t first, int64_t count,
+                              void* dst, size_t cap);
+
+/* Formula text of entry `index` of level k (host buffer of cap bytes). */
+lsyn_status lsyn_entry_formula(lsyn_ctx* ctx, int32_t k, int64_t index, char* buf, size_t cap);
+
+/*
+ * Evaluate a formula on every trace of a problem (the bitwise operators on the
+ * device). dst (host) receives n_pos + n_neg words of word_bits bits: the
+ * formula's CM. config may be NULL (defaults). Errors: LSYN_E_INVAL on a parse
+ * error, an atom >= n_props or more than 4096 nodes.
+ */
+lsyn_status lsyn_eval(const lsyn_problem* problem, const char* formula, void* dst,
+                      const lsyn_config* config);
+
+/*
+ * Host-only helper (no GPU needed): the number of candidates level k builds
+ * when every level i < k holds level_sizes[i - 1] entries (k >= 2; and/or
+ * counted once per unordered pair, U per ordered pair, unary once per entry).
+ */
+int64_t lsyn_level_candidates(const int64_t* level_sizes, int32_t k, uint32_t op_mask);
+
+/* Library version string. */
+const char* lsyn_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LSYN_H_ */

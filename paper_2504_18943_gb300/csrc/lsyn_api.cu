@@ -1,0 +1,824 @@
+// Host side of the lsyn C ABI (include/lsyn.h): context and memory layout,
+// the level schedule of the bottom-up enumeration, solve, export and eval.
+//
+// The level loop follows the listing of paragraph "A generic program
+// synthesiser" (section "Program synthesis"): level 1 is the distinct atoms;
+// level k applies every unary operator to level k-1 and every binary operator
+// to every split {i, j} with i + j = k - 1, checks every candidate against the
+// specification and caches the new characteristic matrices. All of it runs in
+// the kernels of lsyn_device.cuh; the host only plans launches and reads a
+// few counters back per level.
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lsyn.h"
+#include "lsyn_internal.h"
+
+using namespace lsyn;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct Alloc {
+  lsyn_alloc_fn alloc = nullptr;
+  lsyn_free_fn free = nullptr;
+  void* user = nullptr;
+  std::vector<void*> owned;
+  void* get(size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    void* p = nullptr;
+    if (alloc) {
+      p = alloc(bytes, user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+    if (p) owned.push_back(p);
+    return p;
+  }
+  void release_all() {
+    for (void* p : owned) {
+      if (free) free(p, user);
+      else cudaFree(p);
+    }
+    owned.clear();
+  }
+};
+
+uint32_t mix32(uint32_t x) {
+  x ^= x >> 16; x *= 0x7FEB352Du; x ^= x >> 15; x *= 0x846CA68Bu; x ^= x >> 16;
+  return x;
+}
+
+double now_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct Snap {
+  DevCounters c;
+};
+
+}  // namespace
+
+struct lsyn_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  Alloc mem;
+  uint32_t op_mask = LSYN_OPS_ALL;
+  bool full_levels = false;
+  bool timing = false;
+  // problem
+  int n_props = 0, n_pos = 0, n_neg = 0, T = 0, word_bits = 32, max_len = 1, steps = 0;
+  unsigned vecs = 0;
+  int path = 0;
+  int sms = 1;
+  // device memory
+  uint4* arena = nullptr;
+  unsigned long long* prov = nullptr;
+  unsigned long long* table = nullptr;
+  unsigned long long table_cap = 0;
+  unsigned max_entries = 0;
+  DevCounters* ctr = nullptr;
+  uint4* consts = nullptr;  // [5][vecs]: lenmask, label, care, key, mul
+  uint4* atoms = nullptr;   // [n_props][vecs]
+  unsigned long long* defer[2] = {nullptr, nullptr};
+  unsigned defer_cap = 0;
+  char* fbuf = nullptr;
+  int* fstatus = nullptr;
+  static constexpr unsigned kFormulaCap = 1u << 16;
+  // host mirrors
+  Snap* h_snap = nullptr;  // pinned, kSnaps entries
+  static constexpr int kSnaps = 80;
+  char* h_fbuf = nullptr;  // pinned formula text
+  int* h_fstatus = nullptr;
+  std::vector<uint32_t> level_start, level_n;  // indexed by level
+  int levels_done = 0;
+  bool last_incomplete = false;
+  unsigned long long constructed = 0;
+  unsigned long long last_sol = ~0ull;
+  cudaEvent_t ev[2 * 80] = {};
+  bool events_ready = false;
+  std::string err;
+
+  lsyn_status fail(lsyn_status s, const std::string& msg) {
+    err = msg;
+    return s;
+  }
+  lsyn_status cuda_fail(cudaError_t e, const char* where) {
+    err = std::string(where) + ": " + cudaGetErrorString(e);
+    return LSYN_E_CUDA;
+  }
+  CacheView view(unsigned long long* defer_out, unsigned* defer_out_n) const {
+    CacheView cv;
+    cv.arena = arena;
+    cv.prov = prov;
+    cv.table = table;
+    cv.table_mask = table_cap - 1;
+    cv.max_entries = max_entries;
+    cv.vecs = vecs;
+    cv.ctr = ctr;
+    cv.lenmask = consts;
+    cv.label = consts + vecs;
+    cv.care = consts + 2 * vecs;
+    cv.hkey = consts + 3 * vecs;
+    cv.hmul = consts + 4 * vecs;
+    cv.atoms = atoms;
+    cv.defer_out = defer_out;
+    cv.defer_out_n = defer_out_n;
+    cv.defer_cap = defer_cap;
+    cv.steps = steps;
+    cv.early_exit = full_levels ? 0 : 1;
+    return cv;
+  }
+};
+
+namespace {
+
+__global__ void k_level_begin(DevCounters* c) {
+  c->full = 0;
+  c->solved = 0;
+  c->error = 0;
+  c->defer_n[0] = 0;
+  c->defer_n[1] = 0;
+  c->defer_overflow = 0;
+  c->built = 0;
+  for (int i = 0; i < 8; ++i) c->work[i] = 0;
+  c->sol = ~0ull;
+}
+
+__global__ void k_reconstruct(const unsigned long long* prov, unsigned long long root,
+                              const unsigned long long* root_ptr, char* buf, unsigned cap, int* status) {
+  const char kOp[8] = {'p', '!', '&', '|', 'X', 'F', 'G', 'U'};
+  struct Frame {
+    unsigned long long d;
+    int stage;
+  };
+  Frame st[80];
+  int sp = 0;
+  unsigned n = 0;
+  int bad = 0;
+  st[sp++] = {root_ptr ? *root_ptr : root, 0};
+  auto put = [&](char ch) {
+    if (n + 1 < cap) buf[n++] = ch;
+    else bad = 1;
+  };
+  while (sp > 0 && !bad) {
+    Frame& f = st[sp - 1];
+    const unsigned op = desc_op(f.d);
+    if (op == kAtom) {
+      put('p');
+      char tmp[12];
+      int m = 0;
+      unsigned v = desc_left(f.d);
+      do { tmp[m++] = char('0' + v % 10); v /= 10; } while (v);
+      while (m) put(tmp[--m]);
+      --sp;
+      continue;
+    }
+    const bool bin = op == kAnd || op == kOr || op == kUntil;
+    if (f.stage == 0) {
+      put('(');
+      put(kOp[op & 7]);
+      put(' ');
+      f.stage = 1;
+      if (sp >= 80) { bad = 2; break; }
+      st[sp++] = {prov[desc_left(f.d)], 0};
+    } else if (f.stage == 1 && bin) {
+      put(' ');
+      f.stage = 2;
+      if (sp >= 80) { bad = 2; break; }
+      st[sp++] = {prov[desc_right(f.d)], 0};
+    } else {
+      put(')');
+      --sp;
+    }
+  }
+  buf[n < cap ? n : cap - 1] = '\0';
+  *status = bad;
+}
+
+// Candidates built at level k given the sizes of levels 1..k-1 (sizes[i-1]).
+int64_t level_candidates(const int64_t* sizes, int k, uint32_t mask) {
+  if (k < 2) return 0;
+  const int nu = !!(mask & LSYN_OP_NOT) + !!(mask & LSYN_OP_X) + !!(mask & LSYN_OP_F) + !!(mask & LSYN_OP_G);
+  const int nb = !!(mask & LSYN_OP_AND) + !!(mask & LSYN_OP_OR) + 2 * !!(mask & LSYN_OP_U);
+  int64_t c = int64_t(nu) * sizes[k - 2];
+  for (int i = 1; 2 * i <= k - 1; ++i) {
+    const int j = k - 1 - i;
+    const int64_t a = sizes[i - 1], b = sizes[j - 1];
+    c += nb * (i == j ? a * (a - 1) / 2 : a * b);
+  }
+  return c;
+}
+
+lsyn_status launch_desc(lsyn_ctx* c, const CacheView& cv, const unsigned long long* list, const unsigned* list_n,
+                        unsigned n, unsigned atoms, const LaunchCfg& lc) {
+  cudaError_t e = c->word_bits == 32 ? Kernels<uint32_t>::desc_list(cv, list, list_n, n, atoms, lc)
+                                     : Kernels<uint64_t>::desc_list(cv, list, list_n, n, atoms, lc);
+  return e == cudaSuccess ? LSYN_OK : c->cuda_fail(e, "desc kernel");
+}
+
+lsyn_status reconstruct(lsyn_ctx* c, const unsigned long long* root_ptr, char* out, size_t cap) {
+  k_reconstruct<<<1, 1, 0, c->stream>>>(c->prov, 0, root_ptr, c->fbuf, lsyn_ctx::kFormulaCap, c->fstatus);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return c->cuda_fail(e, "reconstruct");
+  e = cudaMemcpyAsync(c->h_fbuf, c->fbuf, lsyn_ctx::kFormulaCap, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_fstatus, c->fstatus, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return c->cuda_fail(e, "reconstruct copy");
+  if (*c->h_fstatus != 0) return c->fail(LSYN_E_STATE, "formula too deep or too long to print");
+  const size_t len = strnlen(c->h_fbuf, lsyn_ctx::kFormulaCap);
+  if (!out || len + 1 > cap) return c->fail(LSYN_E_INVAL, "formula buffer too small");
+  memcpy(out, c->h_fbuf, len + 1);
+  return LSYN_OK;
+}
+
+// Parse prefix formula text into a postorder node list (children first).
+bool parse_formula(const char* s, int n_props, std::vector<int4>* nodes, std::string* err) {
+  size_t i = 0;
+  const size_t len = strlen(s);
+  struct P {
+    const char* s;
+    size_t len;
+    size_t& i;
+    int n_props;
+    std::vector<int4>* nodes;
+    std::string* err;
+    int depth = 0;
+    void skip() { while (i < len && (s[i] == ' ' || s[i] == '\t' || s[i] == '\n')) ++i; }
+    int parse() {
+      if (++depth > 4096 || nodes->size() > 4096) { *err = "formula too large"; return -1; }
+      skip();
+      if (i < len && s[i] == 'p') {
+        ++i;
+        if (i >= len || s[i] < '0' || s[i] > '9') { *err = "bad atom"; return -1; }
+        long v = 0;
+        while (i < len && s[i] >= '0' && s[i] <= '9') { v = v * 10 + (s[i] - '0'); if (v > 1000) break; ++i; }
+        if (v >= n_props) { *err = "atom out of range"; return -1; }
+        nodes->push_back(make_int4(int(kAtom), -1, -1, int(v)));
+        --depth;
+        return int(nodes->size()) - 1;
+      }
+      if (i >= len || s[i] != '(') { *err = "expected '(' or atom"; return -1; }
+      ++i;
+      skip();
+      if (i >= len) { *err = "truncated"; return -1; }
+      int op = -1;
+      switch (s[i]) {
+        case '!': op = kNot; break;
+        case '&': op = kAnd; break;
+        case '|': op = kOr; break;
+        case 'X': op = kNext; break;
+        case 'F': op = kFuture; break;
+        case 'G': op = kGlobally; break;
+        case 'U': op = kUntil; break;
+        default: *err = "unknown operator"; return -1;
+      }
+      ++i;
+      const int a = parse();
+      if (a < 0) return -1;
+      int b = -1;
+      if (op == kAnd || op == kOr || op == kUntil) {
+        b = parse();
+        if (b < 0) return -1;
+      }
+      skip();
+      if (i >= len || s[i] != ')') { *err = "expected ')'"; return -1; }
+      ++i;
+      nodes->push_back(make_int4(op, a, b, 0));
+      --depth;
+      return int(nodes->size()) - 1;
+    }
+  } p{s, len, i, n_props, nodes, err};
+  if (p.parse() < 0) return false;
+  p.skip();
+  if (i != len) { *err = "trailing text"; return false; }
+  return true;
+}
+
+struct Layout {
+  int T = 0, word_bits = 0, max_len = 0, steps = 0;
+  unsigned vecs_needed = 0;
+};
+
+lsyn_status validate(const lsyn_problem* p, Layout* L, std::string* err) {
+  if (!p) { *err = "problem is NULL"; return LSYN_E_INVAL; }
+  if (p->n_props < 1 || p->n_props > 32) { *err = "n_props must be in 1..32"; return LSYN_E_INVAL; }
+  if (p->n_pos < 0 || p->n_neg < 0 || p->n_pos + p->n_neg < 1) { *err = "need n_pos, n_neg >= 0 and at least one trace"; return LSYN_E_INVAL; }
+  if (p->word_bits != 32 && p->word_bits != 64) { *err = "word_bits must be 32 or 64"; return LSYN_E_INVAL; }
+  if (!p->lengths || !p->atom_words) { *err = "lengths and atom_words are required"; return LSYN_E_INVAL; }
+  L->T = p->n_pos + p->n_neg;
+  if (L->T > (1 << 24)) { *err = "too many traces"; return LSYN_E_INVAL; }
+  L->word_bits = p->word_bits;
+  L->max_len = 1;
+  for (int i = 0; i < L->T; ++i) {
+    if (p->lengths[i] < 1 || p->lengths[i] > p->word_bits) {
+      *err = "trace " + std::to_string(i) + " has a length outside 1..word_bits";
+      return LSYN_E_INVAL;
+    }
+    L->max_len = std::max(L->max_len, int(p->lengths[i]));
+  }
+  L->steps = 0;
+  while ((1 << L->steps) < L->max_len) ++L->steps;
+  L->vecs_needed = unsigned((size_t(L->T) * (p->word_bits / 8) + 15) / 16);
+  return LSYN_OK;
+}
+
+// Pack the padded per-word constants and atom rows on the host.
+void pack_host(const lsyn_problem* p, const Layout& L, unsigned vecs, std::vector<uint32_t>* consts,
+               std::vector<uint32_t>* atoms) {
+  const unsigned n32 = vecs * 4;  // 32-bit words per padded CM
+  consts->assign(size_t(5) * n32, 0u);
+  atoms->assign(size_t(p->n_props) * n32, 0u);
+  uint32_t* lm = consts->data();
+  uint32_t* lab = lm + n32;
+  uint32_t* care = lab + n32;
+  uint32_t* key = care + n32;
+  uint32_t* mul = key + n32;
+  const int per = p->word_bits / 32;  // 32-bit halves per word
+  for (int i = 0; i < L.T; ++i) {
+    const int len = p->lengths[i];
+    uint64_t m = len >= 64 ? ~0ull : ((1ull << len) - 1ull);
+    lm[i * per] = uint32_t(m);
+    if (per == 2) lm[i * per + 1] = uint32_t(m >> 32);
+    lab[i * per] = i < p->n_pos ? 1u : 0u;
+    care[i * per] = 1u;
+    for (int q = 0; q < p->n_props; ++q) {
+      uint64_t w;
+      if (per == 1) w = static_cast<const uint32_t*>(p->atom_words)[size_t(q) * L.T + i];
+      else w = static_cast<const uint64_t*>(p->atom_words)[size_t(q) * L.T + i];
+      w &= m;
+      (*atoms)[size_t(q) * n32 + i * per] = uint32_t(w);
+      if (per == 2) (*atoms)[size_t(q) * n32 + i * per + 1] = uint32_t(w >> 32);
+    }
+  }
+  for (unsigned i = 0; i < n32; ++i) {
+    key[i] = mix32(i * 2u + 0x51ED270Bu);
+    mul[i] = mix32(i * 2u + 0x2545F491u) | 1u;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lsyn_version(void) { return "lsyn 0.1 (sm_103a)"; }
+
+int64_t lsyn_level_candidates(const int64_t* level_sizes, int32_t k, uint32_t op_mask) {
+  if (!level_sizes || k < 2) return 0;
+  return level_candidates(level_sizes, k, op_mask ? op_mask : LSYN_OPS_ALL);
+}
+
+const char* lsyn_last_error(const lsyn_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+void lsyn_destroy(lsyn_ctx* c) {
+  if (!c) return;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  if (c->events_ready)
+    for (auto& e : c->ev) if (e) cudaEventDestroy(e);
+  c->mem.release_all();
+  if (c->h_snap) cudaFreeHost(c->h_snap);
+  if (c->h_fbuf) cudaFreeHost(c->h_fbuf);
+  if (c->h_fstatus) cudaFreeHost(c->h_fstatus);
+  if (prev >= 0) cudaSetDevice(prev);
+  delete c;
+}
+
+lsyn_status lsyn_create(const lsyn_problem* problem, const lsyn_config* config, lsyn_ctx** out) {
+  g_create_error.clear();
+  if (!out) { g_create_error = "out is NULL"; return LSYN_E_INVAL; }
+  *out = nullptr;
+  Layout L;
+  lsyn_status s = validate(problem, &L, &g_create_error);
+  if (s != LSYN_OK) return s;
+  lsyn_config cfg;
+  memset(&cfg, 0, sizeof(cfg));
+  cfg.device = -1;
+  if (config) cfg = *config;
+  const uint32_t mask = cfg.op_mask ? cfg.op_mask : LSYN_OPS_ALL;
+  if (mask & ~LSYN_OPS_ALL) { g_create_error = "unknown operator bits"; return LSYN_E_INVAL; }
+  const double load = cfg.table_load > 0 ? cfg.table_load : 0.5;
+  if (!(load > 0 && load <= 0.9)) { g_create_error = "table_load must be in (0, 0.9]"; return LSYN_E_INVAL; }
+  const unsigned long long cache_bytes = cfg.cache_bytes ? cfg.cache_bytes : (1ull << 30);
+
+  unsigned vecs = 0;
+  if (L.vecs_needed <= 8) {
+    vecs = 1;
+    while (vecs < L.vecs_needed) vecs <<= 1;
+  } else if (L.vecs_needed <= 256) {
+    unsigned rv = 1;
+    while (32 * rv < L.vecs_needed) rv <<= 1;
+    vecs = 32 * rv;
+  } else {
+    g_create_error = "characteristic matrices above 4 KiB (" + std::to_string(L.vecs_needed * 16) +
+                     " bytes) are not supported by this build";
+    return LSYN_E_UNSUPPORTED;
+  }
+  const size_t M = size_t(vecs) * 16;
+  // Hash-table capacity (a power of two) and arena entries within the budget,
+  // at most `load` slots in use.
+  unsigned long long best_cap = 0, best_e = 0;
+  for (unsigned long long cap = 1024; cap <= (1ull << 34); cap <<= 1) {
+    if (cap * 8 >= cache_bytes) break;
+    unsigned long long e = (cache_bytes - cap * 8) / (M + 8);
+    e = std::min<unsigned long long>(e, (unsigned long long)(double(cap) * load));
+    e = std::min<unsigned long long>(e, kMaxEntries);
+    if (e > best_e) { best_e = e; best_cap = cap; }
+  }
+  if (best_e < 64) { g_create_error = "cache_bytes too small"; return LSYN_E_INVAL; }
+
+  lsyn_ctx* c = new (std::nothrow) lsyn_ctx;
+  if (!c) { g_create_error = "out of host memory"; return LSYN_E_NOMEM; }
+  c->op_mask = mask;
+  c->full_levels = cfg.full_levels != 0;
+  c->timing = cfg.timing != 0;
+  c->mem.alloc = cfg.alloc;
+  c->mem.free = cfg.free;
+  c->mem.user = cfg.alloc_user;
+  c->stream = static_cast<cudaStream_t>(cfg.stream);
+  c->n_props = problem->n_props;
+  c->n_pos = problem->n_pos;
+  c->n_neg = problem->n_neg;
+  c->T = L.T;
+  c->word_bits = L.word_bits;
+  c->max_len = L.max_len;
+  c->steps = L.steps;
+  c->vecs = vecs;
+  c->path = L.vecs_needed <= 8 ? 1 : 2;
+  c->table_cap = best_cap;
+  c->max_entries = unsigned(best_e);
+  c->defer_cap = 1u << 20;
+
+  auto bail = [&](lsyn_status st, const std::string& msg) {
+    g_create_error = msg;
+    lsyn_destroy(c);
+    return st;
+  };
+  cudaError_t e;
+  if (cfg.device >= 0) {
+    if ((e = cudaSetDevice(cfg.device)) != cudaSuccess) return bail(LSYN_E_CUDA, cudaGetErrorString(e));
+  }
+  if ((e = cudaGetDevice(&c->device)) != cudaSuccess) return bail(LSYN_E_CUDA, cudaGetErrorString(e));
+  cudaDeviceProp prop;
+  if ((e = cudaGetDeviceProperties(&prop, c->device)) != cudaSuccess) return bail(LSYN_E_CUDA, cudaGetErrorString(e));
+  c->sms = prop.multiProcessorCount;
+
+  c->arena = static_cast<uint4*>(c->mem.get(size_t(c->max_entries) * M));
+  c->prov = static_cast<unsigned long long*>(c->mem.get(size_t(c->max_entries) * 8));
+  c->table = static_cast<unsigned long long*>(c->mem.get(size_t(c->table_cap) * 8));
+  c->ctr = static_cast<DevCounters*>(c->mem.get(sizeof(DevCounters)));
+  c->consts = static_cast<uint4*>(c->mem.get(size_t(5) * M));
+  c->atoms = static_cast<uint4*>(c->mem.get(size_t(c->n_props) * M));
+  c->defer[0] = static_cast<unsigned long long*>(c->mem.get(size_t(c->defer_cap) * 8));
+  c->defer[1] = static_cast<unsigned long long*>(c->mem.get(size_t(c->defer_cap) * 8));
+  c->fbuf = static_cast<char*>(c->mem.get(lsyn_ctx::kFormulaCap));
+  c->fstatus = static_cast<int*>(c->mem.get(sizeof(int)));
+  if (!c->arena || !c->prov || !c->table || !c->ctr || !c->consts || !c->atoms || !c->defer[0] || !c->defer[1] ||
+      !c->fbuf || !c->fstatus)
+    return bail(LSYN_E_NOMEM, "device allocation failed");
+  if (cudaMallocHost(&c->h_snap, sizeof(Snap) * lsyn_ctx::kSnaps) != cudaSuccess ||
+      cudaMallocHost(&c->h_fbuf, lsyn_ctx::kFormulaCap) != cudaSuccess ||
+      cudaMallocHost(&c->h_fstatus, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(LSYN_E_NOMEM, "pinned host allocation failed");
+  }
+  for (auto& ev : c->ev)
+    if ((e = cudaEventCreate(&ev)) != cudaSuccess) return bail(LSYN_E_CUDA, cudaGetErrorString(e));
+  c->events_ready = true;
+
+  std::vector<uint32_t> consts, atoms;
+  pack_host(problem, L, vecs, &consts, &atoms);
+  e = cudaMemcpyAsync(c->consts, consts.data(), consts.size() * 4, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->atoms, atoms.data(), atoms.size() * 4, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);  // host vectors go out of scope
+  if (e != cudaSuccess) return bail(LSYN_E_CUDA, cudaGetErrorString(e));
+  s = lsyn_reset(c);
+  if (s != LSYN_OK) return bail(s, c->err);
+  *out = c;
+  return LSYN_OK;
+}
+
+lsyn_status lsyn_reset(lsyn_ctx* c) {
+  if (!c) return LSYN_E_INVAL;
+  cudaSetDevice(c->device);
+  cudaError_t e = cudaMemsetAsync(c->table, 0, size_t(c->table_cap) * 8, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->ctr, 0, sizeof(DevCounters), c->stream);
+  if (e != cudaSuccess) return c->cuda_fail(e, "reset");
+  c->level_start.assign(1, 0);
+  c->level_n.assign(1, 0);
+  c->levels_done = 0;
+  c->last_incomplete = false;
+  c->constructed = 0;
+  c->last_sol = ~0ull;
+  return LSYN_OK;
+}
+
+lsyn_status lsyn_enumerate_level(lsyn_ctx* c, int32_t k, lsyn_level_stats* out) {
+  if (!c) return LSYN_E_INVAL;
+  if (k != c->levels_done + 1) return c->fail(LSYN_E_STATE, "level k must be levels_done + 1");
+  if (c->last_incomplete) return c->fail(LSYN_E_STATE, "the previous level is incomplete (cache full or stopped early)");
+  if (k > 64) return c->fail(LSYN_E_INVAL, "levels above 64 are not supported");
+  cudaSetDevice(c->device);
+  const double t0 = now_ms();
+  LaunchCfg lc{c->stream, c->sms};
+  int snap = 0, evn = 0;
+  int ev_kind[lsyn_ctx::kSnaps];
+  cudaError_t e;
+  auto take_snap = [&]() -> cudaError_t {
+    if (snap >= lsyn_ctx::kSnaps) return cudaErrorInvalidValue;
+    return cudaMemcpyAsync(&c->h_snap[snap++].c, c->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, c->stream);
+  };
+  auto ev_begin = [&]() { if (c->timing) cudaEventRecord(c->ev[2 * evn], c->stream); };
+  auto ev_end = [&](int kind) {
+    if (c->timing) { cudaEventRecord(c->ev[2 * evn + 1], c->stream); ev_kind[evn] = kind; }
+    ++evn;
+  };
+
+  const uint32_t start = c->level_start.back() + c->level_n.back();
+  int launches = 0;
+  ev_begin();
+  k_level_begin<<<1, 1, 0, c->stream>>>(c->ctr);
+  ++launches;
+  if ((e = cudaGetLastError()) != cudaSuccess) return c->cuda_fail(e, "level begin");
+  ev_end(3);
+  if ((e = take_snap()) != cudaSuccess) return c->cuda_fail(e, "snapshot");  // snap 0: before work
+
+  CacheView cv = c->view(c->defer[0], &c->ctr->defer_n[0]);
+  int binary_snap = -1;
+  double op_bytes_unary = 0, op_bytes_binary = 0;
+  const double M = double(c->vecs) * 16.0;
+  if (k == 1) {
+    ev_begin();
+    lsyn_status s = launch_desc(c, cv, nullptr, nullptr, 0, unsigned(c->n_props), lc);
+    ++launches;
+    if (s != LSYN_OK) return s;
+    ev_end(3);
+    if ((e = take_snap()) != cudaSuccess) return c->cuda_fail(e, "snapshot");
+    op_bytes_unary = double(c->n_props) * M;
+  } else {
+    const uint32_t m = c->op_mask;
+    const uint32_t uops = ((m & LSYN_OP_NOT) ? 1u : 0u) | ((m & LSYN_OP_X) ? 2u : 0u) |
+                          ((m & LSYN_OP_F) ? 4u : 0u) | ((m & LSYN_OP_G) ? 8u : 0u);
+    const uint32_t prev_n = c->level_n[k - 1];
+    if (uops && prev_n) {
+      ev_begin();
+      e = c->word_bits == 32 ? Kernels<uint32_t>::unary(cv, c->level_start[k - 1], prev_n, uops, lc)
+                             : Kernels<uint64_t>::unary(cv, c->level_start[k - 1], prev_n, uops, lc);
+      ++launches;
+      if (e != cudaSuccess) return c->cuda_fail(e, "unary kernel");
+      ev_end(0);
+      if ((e = take_snap()) != cudaSuccess) return c->cuda_fail(e, "snapshot");
+      op_bytes_unary = double(prev_n) * M;
+    }
+    const uint32_t bops = ((m & LSYN_OP_AND) ? 1u : 0u) | ((m & LSYN_OP_OR) ? 2u : 0u) | ((m & LSYN_OP_U) ? 12u : 0u);
+    if (bops && k >= 3) {
+      BinaryPlan plan;
+      memset(&plan, 0, sizeof(plan));
+      plan.ops = bops;
+      plan.work_slot = 0;
+      plan.tile = c->path == 2 ? std::max(1u, std::min(32u, unsigned((64 * 1024) / (c->vecs * 16)))) : 1u;
+      unsigned long long tiles = 0, pairs = 0;
+      for (int i = 1; 2 * i <= k - 1; ++i) {
+        const int j = k - 1 - i;
+        const uint32_t ni = c->level_n[i], nj = c->level_n[j];
+        if (!ni || !nj || (i == j && ni < 2)) continue;
+        Split sp;
+        memset(&sp, 0, sizeof(sp));
+        if (i == j || ni <= nj) {
+          sp.left_start = c->level_start[i]; sp.left_n = ni;
+          sp.right_start = c->level_start[j]; sp.right_n = nj;
+        } else {
+          sp.left_start = c->level_start[j]; sp.left_n = nj;
+          sp.right_start = c->level_start[i]; sp.right_n = ni;
+        }
+        sp.tri = i == j ? 1u : 0u;
+        sp.lt_tiles = (sp.left_n + plan.tile - 1) / plan.tile;
+        sp.rt_tiles = (sp.right_n + plan.tile - 1) / plan.tile;
+        sp.tiles_begin = tiles;
+        sp.pairs_begin = pairs;
+        sp.pairs = (unsigned long long)sp.left_n * sp.right_n;
+        tiles += (unsigned long long)sp.lt_tiles * sp.rt_tiles;
+        pairs += sp.pairs;
+        op_bytes_binary += double(sp.left_n + (sp.tri ? 0u : sp.right_n)) * M;
+        plan.s[plan.n_splits++] = sp;
+      }
+      plan.total_tiles = tiles;
+      plan.total_pairs = pairs;
+      if (plan.n_splits > 0) {
+        ev_begin();
+        e = c->word_bits == 32 ? Kernels<uint32_t>::binary(cv, plan, lc) : Kernels<uint64_t>::binary(cv, plan, lc);
+        ++launches;
+        if (e != cudaSuccess) return c->cuda_fail(e, "binary kernel");
+        ev_end(1);
+        if ((e = take_snap()) != cudaSuccess) return c->cuda_fail(e, "snapshot");
+        binary_snap = snap - 1;
+      }
+    }
+  }
+  if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return c->cuda_fail(e, "level sync");
+
+  // Deferred candidates: re-examine them until none is left (ping-pong lists).
+  unsigned long long deferred = 0;
+  int cur = 0;
+  for (int pass = 0;; ++pass) {
+    const DevCounters& h = c->h_snap[snap - 1].c;
+    if (h.defer_overflow) return c->fail(LSYN_E_STATE, "deferred list overflow: the level is not exact");
+    if (h.error) return c->fail(LSYN_E_STATE, "hash table probe overflow");
+    const unsigned n = std::min(h.defer_n[cur], c->defer_cap);
+    if (n == 0) break;
+    if (pass >= 48) return c->fail(LSYN_E_STATE, "deferred candidates did not settle");
+    deferred += n;
+    if ((e = cudaMemsetAsync(&c->ctr->defer_n[1 - cur], 0, sizeof(unsigned), c->stream)) != cudaSuccess)
+      return c->cuda_fail(e, "memset");
+    CacheView rv = c->view(c->defer[1 - cur], &c->ctr->defer_n[1 - cur]);
+    rv.early_exit = 0;  // a deferred candidate must be settled even after a solution
+    ev_begin();
+    lsyn_status s = launch_desc(c, rv, c->defer[cur], &c->ctr->defer_n[cur], n, 0, lc);
+    ++launches;
+    if (s != LSYN_OK) return s;
+    ev_end(2);
+    if ((e = take_snap()) != cudaSuccess) return c->cuda_fail(e, "snapshot");
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return c->cuda_fail(e, "resolve sync");
+    cur = 1 - cur;
+  }
+  const DevCounters& h = c->h_snap[snap - 1].c;
+  if (h.error) return c->fail(LSYN_E_STATE, "hash table probe overflow");
+  const uint32_t total = std::min(h.n_entries, c->max_entries);
+  const uint32_t unique = total - start;
+  c->level_start.push_back(start);
+  c->level_n.push_back(unique);
+  c->levels_done = k;
+  std::vector<int64_t> sizes(c->level_n.begin() + 1, c->level_n.end());
+  const int64_t planned = k == 1 ? c->n_props : level_candidates(sizes.data(), k, c->op_mask);
+  const bool stopped = h.solved && c->full_levels == false && int64_t(h.built) < planned;
+  c->last_incomplete = h.full || stopped;
+  c->constructed += h.built;
+  c->last_sol = h.solved ? h.sol : ~0ull;
+
+  if (out) {
+    memset(out, 0, sizeof(*out));
+    out->level = k;
+    out->solved = h.solved ? 1 : 0;
+    out->cache_full = h.full ? 1 : 0;
+    out->early_exit = stopped ? 1 : 0;
+    out->candidates = int64_t(h.built);
+    out->unique = unique;
+    out->total = total;
+    out->deferred = int64_t(deferred);
+    out->launches = launches;
+    const double C = double(h.built), U = double(unique);
+    out->bytes_alg = op_bytes_unary + op_bytes_binary + C * 32.0 + (C - U) * M + U * (M + 16.0);
+    if (binary_snap >= 0) {
+      const DevCounters& b0 = c->h_snap[binary_snap - 1].c;
+      const DevCounters& b1 = c->h_snap[binary_snap].c;
+      const double Cb = double(b1.built - b0.built);
+      const double Ub = double(std::min(b1.n_entries, c->max_entries) - std::min(b0.n_entries, c->max_entries));
+      out->bytes_binary = op_bytes_binary + Cb * 32.0 + (Cb - Ub) * M + Ub * (M + 16.0);
+    }
+    if (c->timing) {
+      for (int i = 0; i < evn; ++i) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, c->ev[2 * i], c->ev[2 * i + 1]) == cudaSuccess) out->kernel_ms[ev_kind[i]] += ms;
+      }
+    }
+    out->ms = now_ms() - t0;
+  }
+  return LSYN_OK;
+}
+
+lsyn_status lsyn_solve(lsyn_ctx* c, int32_t max_size, lsyn_result* out) {
+  if (!c || !out) return LSYN_E_INVAL;
+  if (max_size < 1 || max_size > 64) return c->fail(LSYN_E_INVAL, "max_size must be in 1..64");
+  const double t0 = now_ms();
+  out->found = 0;
+  out->size = 0;
+  out->exact = 0;
+  out->launches = 0;
+  lsyn_status result = LSYN_NOT_FOUND;
+  for (int k = c->levels_done + 1; k <= max_size; ++k) {
+    lsyn_level_stats st;
+    lsyn_status s = lsyn_enumerate_level(c, k, &st);
+    if (s != LSYN_OK) { result = s; break; }
+    out->launches += st.launches;
+    if (out->level_stats && k <= out->level_stats_cap) out->level_stats[k - 1] = st;
+    if (st.solved) {
+      out->launches += 1;
+      s = reconstruct(c, &c->ctr->sol, out->formula, out->formula_cap);
+      if (s != LSYN_OK) { result = s; break; }
+      out->found = 1;
+      out->size = k;
+      out->exact = 1;
+      result = LSYN_OK;
+      break;
+    }
+    if (st.cache_full) {
+      c->err = "language cache full at level " + std::to_string(k);
+      result = LSYN_E_CACHE_FULL;
+      break;
+    }
+  }
+  out->levels_done = c->levels_done;
+  out->constructed = int64_t(c->constructed);
+  out->unique = int64_t(c->level_start.back() + c->level_n.back());
+  out->ms = now_ms() - t0;
+  return result;
+}
+
+lsyn_status lsyn_level_count(const lsyn_ctx* c, int32_t k, int64_t* n_out) {
+  if (!c || !n_out || k < 1 || k > c->levels_done) return LSYN_E_INVAL;
+  *n_out = c->level_n[k];
+  return LSYN_OK;
+}
+
+lsyn_status lsyn_export_level(lsyn_ctx* c, int32_t k, int64_t first, int64_t count, void* dst, size_t cap) {
+  if (!c || k < 1 || k > c->levels_done || first < 0 || count < 0) return LSYN_E_INVAL;
+  if (uint64_t(first) + uint64_t(count) > c->level_n[k]) return c->fail(LSYN_E_INVAL, "range outside the level");
+  const size_t row = size_t(c->T) * (c->word_bits / 8);
+  if (count == 0) return LSYN_OK;
+  if (!dst || cap < row * size_t(count)) return c->fail(LSYN_E_INVAL, "destination too small");
+  cudaSetDevice(c->device);
+  const uint4* src = c->arena + (size_t(c->level_start[k]) + size_t(first)) * c->vecs;
+  cudaError_t e = cudaMemcpy2DAsync(dst, row, src, size_t(c->vecs) * 16, row, size_t(count),
+                                    cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return e == cudaSuccess ? LSYN_OK : c->cuda_fail(e, "export");
+}
+
+lsyn_status lsyn_entry_formula(lsyn_ctx* c, int32_t k, int64_t index, char* buf, size_t cap) {
+  if (!c || k < 1 || k > c->levels_done || index < 0 || uint64_t(index) >= c->level_n[k]) return LSYN_E_INVAL;
+  cudaSetDevice(c->device);
+  return reconstruct(c, c->prov + c->level_start[k] + size_t(index), buf, cap);
+}
+
+lsyn_status lsyn_eval(const lsyn_problem* problem, const char* formula, void* dst, const lsyn_config* config) {
+  g_create_error.clear();
+  Layout L;
+  lsyn_status s = validate(problem, &L, &g_create_error);
+  if (s != LSYN_OK) return s;
+  if (!formula || !dst) { g_create_error = "formula and dst are required"; return LSYN_E_INVAL; }
+  std::vector<int4> nodes;
+  if (!parse_formula(formula, problem->n_props, &nodes, &g_create_error)) return LSYN_E_INVAL;
+  lsyn_config cfg;
+  memset(&cfg, 0, sizeof(cfg));
+  cfg.device = -1;
+  if (config) cfg = *config;
+  if (cfg.device >= 0 && cudaSetDevice(cfg.device) != cudaSuccess) { g_create_error = "bad device"; return LSYN_E_CUDA; }
+  cudaStream_t stream = static_cast<cudaStream_t>(cfg.stream);
+  const unsigned vecs = std::max(1u, L.vecs_needed);
+  const size_t M = size_t(vecs) * 16;
+  std::vector<uint32_t> consts, atoms;
+  pack_host(problem, L, vecs, &consts, &atoms);
+  Alloc mem;
+  mem.alloc = cfg.alloc;
+  mem.free = cfg.free;
+  mem.user = cfg.alloc_user;
+  uint4* d_lm = static_cast<uint4*>(mem.get(M));
+  uint4* d_atoms = static_cast<uint4*>(mem.get(size_t(problem->n_props) * M));
+  int4* d_nodes = static_cast<int4*>(mem.get(nodes.size() * sizeof(int4)));
+  uint4* d_scratch = static_cast<uint4*>(mem.get(nodes.size() * M));
+  uint4* d_out = static_cast<uint4*>(mem.get(M));
+  if (!d_lm || !d_atoms || !d_nodes || !d_scratch || !d_out) {
+    mem.release_all();
+    g_create_error = "device allocation failed";
+    return LSYN_E_NOMEM;
+  }
+  std::vector<uint8_t> host_out(M);
+  LaunchCfg lc{stream, 1};
+  cudaError_t e = cudaMemcpyAsync(d_lm, consts.data(), M, cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_atoms, atoms.data(), atoms.size() * 4, cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_nodes, nodes.data(), nodes.size() * sizeof(int4), cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess) {
+    if (L.word_bits == 32)
+      e = Kernels<uint32_t>::eval(d_atoms, d_lm, vecs, d_nodes, int(nodes.size()), L.steps,
+                                  reinterpret_cast<uint32_t*>(d_scratch), reinterpret_cast<uint32_t*>(d_out), lc);
+    else
+      e = Kernels<uint64_t>::eval(d_atoms, d_lm, vecs, d_nodes, int(nodes.size()), L.steps,
+                                  reinterpret_cast<uint64_t*>(d_scratch), reinterpret_cast<uint64_t*>(d_out), lc);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host_out.data(), d_out, M, cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  mem.release_all();
+  if (e != cudaSuccess) {
+    g_create_error = std::string("eval: ") + cudaGetErrorString(e);
+    return LSYN_E_CUDA;
+  }
+  memcpy(dst, host_out.data(), size_t(L.T) * (L.word_bits / 8));
+  return LSYN_OK;
+}
+
+}  // extern "C"

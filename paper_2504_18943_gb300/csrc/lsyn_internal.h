@@ -1,0 +1,122 @@
+// Internal declarations shared by the host driver (lsyn_api.cu) and the
+// kernel translation units (kernels_w32.cu, kernels_w64.cu).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lsyn {
+
+// Operator codes stored in provenance records.
+enum : uint32_t {
+  kAtom = 0, kNot = 1, kAnd = 2, kOr = 3, kNext = 4, kFuture = 5, kGlobally = 6, kUntil = 7
+};
+
+// A candidate is named by a 64-bit descriptor: op in bits 60..63, the left
+// child's cache id (or the proposition, for atoms) in bits 30..59 and the right
+// child's id in bits 0..29. Cache ids therefore stay below 2^30.
+constexpr uint32_t kIdBits = 30;
+constexpr uint32_t kIdMask = (1u << kIdBits) - 1u;
+constexpr uint32_t kMaxEntries = (1u << kIdBits) - 2u;
+
+__host__ __device__ inline uint64_t pack_desc(uint32_t op, uint32_t left, uint32_t right) {
+  return (uint64_t(op) << 60) | (uint64_t(left & kIdMask) << 30) | uint64_t(right & kIdMask);
+}
+__host__ __device__ inline uint32_t desc_op(uint64_t d) { return uint32_t(d >> 60); }
+__host__ __device__ inline uint32_t desc_left(uint64_t d) { return uint32_t(d >> 30) & kIdMask; }
+__host__ __device__ inline uint32_t desc_right(uint64_t d) { return uint32_t(d) & kIdMask; }
+
+// Hash-table slot: 0 = empty; otherwise tag (high 32 bits of the CM hash) in
+// the high word and, in the low word, id + 1 of a published entry, or one of:
+constexpr uint32_t kSlotPending = 0xFFFFFFFFu;  // claimed, CM not yet published
+constexpr uint32_t kSlotTomb = 0xFFFFFFFEu;     // claimed, but the arena was full
+
+// Device-side counters of one context. The fields from `level_begin` on are
+// cleared at the start of every level.
+struct DevCounters {
+  unsigned int n_entries;        // arena fill (may exceed max_entries when full)
+  unsigned int pad0;
+  unsigned long long sol;        // smallest descriptor of a separating candidate
+  // ---- per level ----
+  unsigned int level_begin;      // marker (unused)
+  unsigned int full;             // an insert found the arena full
+  unsigned int solved;           // a separating candidate was found (early exit flag)
+  unsigned int error;            // probe ran over the whole table (cannot happen at load <= 0.9)
+  unsigned int defer_n[2];       // deferred-list fills (ping-pong)
+  unsigned int defer_overflow;   // a deferred list overflowed: exactness lost
+  unsigned int pad1;
+  unsigned long long built;      // candidates built in this level
+  unsigned long long work[8];    // tile counters of the persistent launches
+};
+
+// Everything a kernel needs to probe, compare and insert (passed by value).
+struct CacheView {
+  uint4* arena;                  // [max_entries][vecs]
+  unsigned long long* prov;      // [max_entries] descriptors
+  unsigned long long* table;     // [table_mask + 1] slots
+  unsigned long long table_mask;
+  unsigned int max_entries;
+  unsigned int vecs;             // 16-byte vectors per CM (padded)
+  DevCounters* ctr;
+  const uint4* lenmask;          // [vecs]: bits 0..len-1 of every trace word
+  const uint4* label;            // [vecs]: bit 0 = 1 for positive traces
+  const uint4* care;             // [vecs]: bit 0 = 1 for real (not padding) traces
+  const uint4* hkey;             // [vecs]: per-32-bit-word hash keys
+  const uint4* hmul;             // [vecs]: per-32-bit-word odd hash multipliers
+  const uint4* atoms;            // [n_props][vecs]
+  unsigned long long* defer_out; // deferred descriptors written by this launch
+  unsigned int* defer_out_n;
+  unsigned int defer_cap;
+  int steps;                     // log-step count: 2^steps >= longest trace
+  int early_exit;                // 1: stop at the first separating candidate
+};
+
+// One split {i, j} of level k (i + j = k - 1) for the binary operators.
+struct Split {
+  uint32_t left_start, left_n;   // rows of the smaller level (staged operand)
+  uint32_t right_start, right_n; // rows of the other level (streamed operand)
+  uint32_t tri;                  // 1 when both sides are the same level: pairs a < b only
+  uint32_t lt_tiles, rt_tiles;   // tiles along each side
+  uint32_t pad;
+  unsigned long long tiles_begin;
+  unsigned long long pairs_begin;
+  unsigned long long pairs;
+};
+
+constexpr int kMaxSplits = 32;
+
+struct BinaryPlan {
+  int n_splits;
+  uint32_t ops;                  // bit 0 and, bit 1 or, bit 2 U(a,b), bit 3 U(b,a)
+  uint32_t tile;                 // rows per tile side (path B)
+  uint32_t work_slot;            // which DevCounters::work counter to use
+  unsigned long long total_tiles;
+  unsigned long long total_pairs;
+  Split s[kMaxSplits];
+};
+
+// Launch parameters chosen by the host.
+struct LaunchCfg {
+  cudaStream_t stream;
+  int sms;                       // multiprocessor count
+};
+
+// Kernel launchers, instantiated for W = uint32_t and uint64_t.
+template <typename W>
+struct Kernels {
+  // Path selection: returns 0 if vecs is not supported.
+  static int path_for(unsigned vecs);
+  // Level 1 (implicit descriptors ATOM 0..n-1) or a deferred list.
+  static cudaError_t desc_list(const CacheView& cv, const unsigned long long* list,
+                               const unsigned int* list_n, unsigned int list_cap,
+                               unsigned int implicit_atoms, const LaunchCfg& lc);
+  static cudaError_t unary(const CacheView& cv, uint32_t first, uint32_t count, uint32_t ops,
+                           const LaunchCfg& lc);
+  static cudaError_t binary(const CacheView& cv, const BinaryPlan& plan, const LaunchCfg& lc);
+  // Evaluate a postorder node list on every trace word: scratch [n_nodes][words].
+  static cudaError_t eval(const uint4* atoms, const uint4* lenmask, unsigned vecs,
+                          const int4* nodes, int n_nodes, int steps, W* scratch, W* out,
+                          const LaunchCfg& lc);
+};
+
+}  // namespace lsyn

@@ -1,0 +1,384 @@
+"""Thin Python binding of the lsyn C ABI (``include/lsyn.h``).
+
+Functions carry the C names and only marshal arguments: every step of the
+enumeration runs in the CUDA library ``_lib/liblsyn.so``. There is no CPU
+fallback: if the library is missing or cannot be loaded, importing this module
+raises. PyTorch serves only as the device allocator and stream provider
+(``torch_config``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+LSYN_OK = 0
+LSYN_NOT_FOUND = 1
+LSYN_PENDING = 2
+LSYN_E_INVAL = -1
+LSYN_E_NOMEM = -2
+LSYN_E_CUDA = -3
+LSYN_E_UNSUPPORTED = -4
+LSYN_E_CACHE_FULL = -5
+LSYN_E_TIMEOUT = -6
+LSYN_E_STATE = -7
+
+OP_NOT, OP_AND, OP_OR, OP_X, OP_F, OP_G, OP_U = (1 << i for i in range(7))
+OPS_ALL = 0x7F
+OPS_PAPER = OP_NOT | OP_AND | OP_X | OP_F | OP_U
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class lsyn_problem(ctypes.Structure):
+    _fields_ = [("n_props", ctypes.c_int32), ("n_pos", ctypes.c_int32), ("n_neg", ctypes.c_int32),
+                ("word_bits", ctypes.c_int32), ("lengths", ctypes.POINTER(ctypes.c_int32)),
+                ("atom_words", ctypes.c_void_p)]
+
+
+class lsyn_config(ctypes.Structure):
+    _fields_ = [("op_mask", ctypes.c_uint32), ("cache_bytes", ctypes.c_uint64), ("table_load", ctypes.c_float),
+                ("full_levels", ctypes.c_int32), ("timing", ctypes.c_int32), ("alloc", ALLOC_FN),
+                ("free", FREE_FN), ("alloc_user", ctypes.c_void_p), ("stream", ctypes.c_void_p),
+                ("device", ctypes.c_int32)]
+
+
+class lsyn_level_stats(ctypes.Structure):
+    _fields_ = [("level", ctypes.c_int32), ("solved", ctypes.c_int32), ("cache_full", ctypes.c_int32),
+                ("early_exit", ctypes.c_int32), ("candidates", ctypes.c_int64), ("unique", ctypes.c_int64),
+                ("total", ctypes.c_int64), ("deferred", ctypes.c_int64), ("ms", ctypes.c_double),
+                ("kernel_ms", ctypes.c_double * 4), ("bytes_alg", ctypes.c_double),
+                ("bytes_binary", ctypes.c_double), ("launches", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("kernel_ms", "reserved")}
+        d["kernel_ms"] = list(self.kernel_ms)
+        return d
+
+
+class lsyn_result(ctypes.Structure):
+    _fields_ = [("found", ctypes.c_int32), ("size", ctypes.c_int32), ("exact", ctypes.c_int32),
+                ("levels_done", ctypes.c_int32), ("constructed", ctypes.c_int64), ("unique", ctypes.c_int64),
+                ("ms", ctypes.c_double), ("launches", ctypes.c_int32), ("level_stats_cap", ctypes.c_int32),
+                ("level_stats", ctypes.POINTER(lsyn_level_stats)), ("formula", ctypes.c_char_p),
+                ("formula_cap", ctypes.c_size_t)]
+
+
+class LsynError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"lsyn status {status}: {message}")
+        self.status = status
+
+
+def _load_library():
+    path = _build.LIB_PATH
+    if not os.path.exists(path):
+        raise ImportError(f"the lsyn CUDA library is not built ({path}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    P, vp, i32, i64 = ctypes.POINTER, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    lib.lsyn_create.restype = i32
+    lib.lsyn_create.argtypes = [P(lsyn_problem), P(lsyn_config), P(vp)]
+    lib.lsyn_destroy.restype = None
+    lib.lsyn_destroy.argtypes = [vp]
+    lib.lsyn_last_error.restype = ctypes.c_char_p
+    lib.lsyn_last_error.argtypes = [vp]
+    lib.lsyn_reset.restype = i32
+    lib.lsyn_reset.argtypes = [vp]
+    lib.lsyn_enumerate_level.restype = i32
+    lib.lsyn_enumerate_level.argtypes = [vp, i32, P(lsyn_level_stats)]
+    lib.lsyn_solve.restype = i32
+    lib.lsyn_solve.argtypes = [vp, i32, P(lsyn_result)]
+    lib.lsyn_level_count.restype = i32
+    lib.lsyn_level_count.argtypes = [vp, i32, P(i64)]
+    lib.lsyn_export_level.restype = i32
+    lib.lsyn_export_level.argtypes = [vp, i32, i64, i64, vp, ctypes.c_size_t]
+    lib.lsyn_entry_formula.restype = i32
+    lib.lsyn_entry_formula.argtypes = [vp, i32, i64, ctypes.c_char_p, ctypes.c_size_t]
+    lib.lsyn_eval.restype = i32
+    lib.lsyn_eval.argtypes = [P(lsyn_problem), ctypes.c_char_p, vp, P(lsyn_config)]
+    lib.lsyn_level_candidates.restype = i64
+    lib.lsyn_level_candidates.argtypes = [P(i64), i32, ctypes.c_uint32]
+    lib.lsyn_version.restype = ctypes.c_char_p
+    lib.lsyn_version.argtypes = []
+    return lib
+
+
+_lib = _load_library()
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def _err(ctx) -> str:
+    m = _lib.lsyn_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def _check(status: int, ctx=None, ok=(LSYN_OK,)) -> int:
+    if status not in ok:
+        raise LsynError(status, _err(ctx))
+    return status
+
+
+# ---------------------------------------------------------------------------
+# Argument marshalling
+# ---------------------------------------------------------------------------
+
+class PackedProblem:
+    """A problem in the ABI layout: atom words [n_props][T] and lengths [T].
+
+    Holds the numpy buffers the ``lsyn_problem`` struct points to."""
+
+    def __init__(self, n_props: int, n_pos: int, n_neg: int, word_bits: int, lengths: np.ndarray,
+                 atom_words: np.ndarray):
+        self.n_props, self.n_pos, self.n_neg, self.word_bits = n_props, n_pos, n_neg, word_bits
+        self.lengths = np.ascontiguousarray(lengths, dtype=np.int32)
+        dt = np.uint32 if word_bits == 32 else np.uint64
+        self.atom_words = np.ascontiguousarray(atom_words, dtype=dt)
+        self.struct = lsyn_problem(n_props, n_pos, n_neg, word_bits,
+                                   self.lengths.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                   self.atom_words.ctypes.data)
+
+    @property
+    def n_traces(self) -> int:
+        return self.n_pos + self.n_neg
+
+    @property
+    def word_dtype(self):
+        return np.uint32 if self.word_bits == 32 else np.uint64
+
+    @property
+    def h2d_bytes(self) -> int:
+        return int(self.lengths.nbytes + self.atom_words.nbytes)
+
+
+def pack_traces(bits: np.ndarray, lengths: np.ndarray, n_pos: int, n_neg: int, word_bits: int) -> PackedProblem:
+    """Pack boolean traces ``bits[i, t, p]`` into atom words (bit t of word (p, i))."""
+    bits = np.asarray(bits, dtype=bool)
+    T, L, n = bits.shape
+    if L > word_bits:
+        if bits[:, word_bits:, :].any():
+            raise ValueError("a trace is longer than the word width")
+        bits = bits[:, :word_bits, :]
+        L = word_bits
+    weights = np.left_shift(np.uint64(1), np.arange(L, dtype=np.uint64))
+    words = (bits.transpose(2, 0, 1).astype(np.uint64) * weights[None, None, :]).sum(axis=2, dtype=np.uint64)
+    return PackedProblem(n, n_pos, n_neg, word_bits, lengths, words)
+
+
+def pack_problem(problem) -> PackedProblem:
+    """Pack a ``workloads.Problem``."""
+    return pack_traces(problem.traces.bits, problem.traces.lengths, problem.n_pos, problem.n_neg,
+                       problem.word_bits)
+
+
+def make_config(op_mask: int = 0, cache_bytes: int = 0, table_load: float = 0.0, full_levels: bool = False,
+                timing: bool = False, stream=None, device: int = -1, allocator=None) -> lsyn_config:
+    cfg = lsyn_config()
+    cfg.op_mask = op_mask
+    cfg.cache_bytes = cache_bytes
+    cfg.table_load = table_load
+    cfg.full_levels = 1 if full_levels else 0
+    cfg.timing = 1 if timing else 0
+    cfg.stream = stream
+    cfg.device = device
+    if allocator is not None:
+        cfg.alloc, cfg.free = allocator.alloc_fn, allocator.free_fn
+    else:
+        cfg.alloc = ALLOC_FN()
+        cfg.free = FREE_FN()
+    cfg._allocator = allocator  # keep the callbacks alive with the struct
+    return cfg
+
+
+class TorchAllocator:
+    """Device allocation through the PyTorch caching allocator on a stream."""
+
+    def __init__(self, device: Optional[int] = None, stream=None):
+        import torch
+        self._torch = torch
+        self.device = torch.cuda.current_device() if device is None else device
+        self.stream = stream
+
+        def _alloc(nbytes, _user):
+            try:
+                return self._torch.cuda.caching_allocator_alloc(int(nbytes), self.device, self.stream)
+            except Exception:  # noqa: BLE001 - reported to the library as NULL
+                return None
+
+        def _free(ptr, _user):
+            if ptr:
+                self._torch.cuda.caching_allocator_delete(ptr)
+
+        self.alloc_fn = ALLOC_FN(_alloc)
+        self.free_fn = FREE_FN(_free)
+
+
+def torch_config(op_mask: int = 0, cache_bytes: int = 0, full_levels: bool = False, timing: bool = False,
+                 stream=None, device: Optional[int] = None, table_load: float = 0.0) -> lsyn_config:
+    """A config whose device memory comes from PyTorch and whose work goes on a torch stream."""
+    import torch
+    dev = torch.cuda.current_device() if device is None else device
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    alloc = TorchAllocator(dev, s)
+    cfg = make_config(op_mask, cache_bytes, table_load, full_levels, timing, s.cuda_stream, dev, alloc)
+    cfg._torch_stream = s
+    return cfg
+
+
+# ---------------------------------------------------------------------------
+# The C entry points, same names
+# ---------------------------------------------------------------------------
+
+def lsyn_version() -> str:
+    return _lib.lsyn_version().decode()
+
+
+def lsyn_create(problem: PackedProblem, config: Optional[lsyn_config] = None) -> ctypes.c_void_p:
+    ctx = ctypes.c_void_p()
+    st = _lib.lsyn_create(ctypes.byref(problem.struct), ctypes.byref(config) if config is not None else None,
+                          ctypes.byref(ctx))
+    _check(st, None)
+    return ctx
+
+
+def lsyn_destroy(ctx) -> None:
+    _lib.lsyn_destroy(ctx)
+
+
+def lsyn_last_error(ctx=None) -> str:
+    return _err(ctx)
+
+
+def lsyn_reset(ctx) -> None:
+    _check(_lib.lsyn_reset(ctx), ctx)
+
+
+def lsyn_enumerate_level(ctx, k: int) -> lsyn_level_stats:
+    st = lsyn_level_stats()
+    _check(_lib.lsyn_enumerate_level(ctx, k, ctypes.byref(st)), ctx)
+    return st
+
+
+def lsyn_solve(ctx, max_size: int, formula_cap: int = 1 << 16):
+    """Returns (status, lsyn_result, formula text or None, per-level stats of
+    the levels this call built); LSYN_NOT_FOUND and LSYN_E_CACHE_FULL are
+    results, not exceptions."""
+    buf = ctypes.create_string_buffer(formula_cap)
+    levels = (lsyn_level_stats * 64)()
+    res = lsyn_result()
+    res.formula = ctypes.cast(buf, ctypes.c_char_p)
+    res.formula_cap = formula_cap
+    res.level_stats = ctypes.cast(levels, ctypes.POINTER(lsyn_level_stats))
+    res.level_stats_cap = 64
+    st = _check(_lib.lsyn_solve(ctx, max_size, ctypes.byref(res)), ctx,
+                ok=(LSYN_OK, LSYN_NOT_FOUND, LSYN_E_CACHE_FULL))
+    text = buf.value.decode() if st == LSYN_OK else None
+    built = [levels[i] for i in range(min(64, res.levels_done)) if levels[i].level == i + 1]
+    return st, res, text, built
+
+
+def lsyn_level_count(ctx, k: int) -> int:
+    n = ctypes.c_int64()
+    _check(_lib.lsyn_level_count(ctx, k, ctypes.byref(n)), ctx)
+    return int(n.value)
+
+
+def lsyn_export_level(ctx, k: int, n_traces: int, word_bits: int, first: int = 0,
+                      count: Optional[int] = None) -> np.ndarray:
+    """CMs of level k as an array [count, n_traces] of uint32/uint64 words."""
+    if count is None:
+        count = lsyn_level_count(ctx, k) - first
+    dt = np.uint32 if word_bits == 32 else np.uint64
+    out = np.empty((count, n_traces), dtype=dt)
+    _check(_lib.lsyn_export_level(ctx, k, first, count, out.ctypes.data if count else None, out.nbytes), ctx)
+    return out
+
+
+def lsyn_entry_formula(ctx, k: int, index: int, cap: int = 1 << 16) -> str:
+    buf = ctypes.create_string_buffer(cap)
+    _check(_lib.lsyn_entry_formula(ctx, k, index, buf, cap), ctx)
+    return buf.value.decode()
+
+
+def lsyn_eval(problem: PackedProblem, formula: str, config: Optional[lsyn_config] = None) -> np.ndarray:
+    out = np.zeros(problem.n_traces, dtype=problem.word_dtype)
+    st = _lib.lsyn_eval(ctypes.byref(problem.struct), formula.encode(), out.ctypes.data,
+                        ctypes.byref(config) if config is not None else None)
+    _check(st, None)
+    return out
+
+
+def lsyn_level_candidates(level_sizes: Sequence[int], k: int, op_mask: int = OPS_ALL) -> int:
+    arr = (ctypes.c_int64 * max(1, len(level_sizes)))(*level_sizes)
+    return int(_lib.lsyn_level_candidates(arr, k, op_mask))
+
+
+# ---------------------------------------------------------------------------
+# Conveniences
+# ---------------------------------------------------------------------------
+
+def labeller(formula: str, traces, n_props: int) -> np.ndarray:
+    """Workload labeller on the GPU: True where trace, 0 |= formula (lsyn_eval)."""
+    p = pack_traces(traces.bits, traces.lengths, len(traces.lengths), 0, 64)
+    cm = lsyn_eval(p, formula)
+    return (cm & np.uint64(1)).astype(bool)
+
+
+def cm_strings(words: np.ndarray, lengths: Sequence[int]) -> str:
+    """One CM row as '0'/'1' characteristic sequences joined by ',' (position 0 first)."""
+    parts = []
+    for w, L in zip(words, lengths):
+        w = int(w)
+        parts.append("".join("1" if (w >> t) & 1 else "0" for t in range(int(L))))
+    return ",".join(parts)
+
+
+class Synthesizer:
+    """Owns one lsyn context: ``with Synthesizer(problem, cfg) as s: s.solve(12)``."""
+
+    def __init__(self, problem: PackedProblem, config: Optional[lsyn_config] = None):
+        self.problem = problem
+        self.config = config
+        self.ctx = lsyn_create(problem, config)
+
+    def close(self):
+        if self.ctx:
+            lsyn_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def level(self, k: int) -> lsyn_level_stats:
+        return lsyn_enumerate_level(self.ctx, k)
+
+    def solve(self, max_size: int):
+        return lsyn_solve(self.ctx, max_size)
+
+    def reset(self):
+        lsyn_reset(self.ctx)
+
+    def count(self, k: int) -> int:
+        return lsyn_level_count(self.ctx, k)
+
+    def export(self, k: int, first: int = 0, count: Optional[int] = None) -> np.ndarray:
+        return lsyn_export_level(self.ctx, k, self.problem.n_traces, self.problem.word_bits, first, count)
+
+    def formula(self, k: int, index: int) -> str:
+        return lsyn_entry_formula(self.ctx, k, index)

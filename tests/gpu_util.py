@@ -1,0 +1,68 @@
+"""Helpers shared by the GPU parity tests: run the CUDA path through the C ABI
+and compare its levels with the CPU oracle's, element by element."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+
+
+def lib():
+    import torch
+    if not torch.cuda.is_available():
+        import pytest
+        pytest.skip("no CUDA GPU")
+    from paper_2504_18943_gb300 import build
+    build.build()
+    from paper_2504_18943_gb300 import lsyn
+    return lsyn
+
+
+def oracle_rows(cms, word_bits: int, n_traces: int) -> np.ndarray:
+    """Oracle CM strings ('0'/'1', position 0 first, traces joined by ',') as words."""
+    dt = np.uint32 if word_bits == 32 else np.uint64
+    out = np.zeros((len(cms), n_traces), dtype=dt)
+    for r, cm in enumerate(cms):
+        seqs = cm.split(",")
+        assert len(seqs) == n_traces
+        out[r] = [int(s[::-1], 2) if s else 0 for s in seqs]
+    return out
+
+
+def canon(rows: np.ndarray) -> np.ndarray:
+    if rows.shape[0] == 0:
+        return rows
+    return np.unique(rows, axis=0)
+
+
+def assert_levels_match(L, problem, depth, op_mask=0x7F, cache_bytes=256 << 20, config=None, spec=None):
+    """GPU levels 1..depth (built completely) equal the oracle's, as sets of CMs,
+    with no duplicate inside a level or across levels."""
+    spec = spec or oracle.Spec.from_problem(problem)
+    run = spec.enumerate(depth, op_mask)
+    packed = L.pack_problem(problem)
+    cfg = config or L.make_config(op_mask=op_mask, full_levels=True, cache_bytes=cache_bytes)
+    seen = []
+    with L.Synthesizer(packed, cfg) as s:
+        for k in range(1, depth + 1):
+            st = s.level(k)
+            assert not st.cache_full, f"cache full at level {k}"
+            rows = s.export(k)
+            assert rows.shape[0] == run.size(k), (k, rows.shape[0], run.size(k))
+            got = canon(rows)
+            assert got.shape[0] == rows.shape[0], f"duplicate CMs inside level {k}"
+            want = canon(oracle_rows(run.cms(k), problem.word_bits, problem.n_traces))
+            assert np.array_equal(got, want), f"level {k} differs from the oracle"
+            seen.append(rows)
+        allrows = np.concatenate(seen) if seen else np.zeros((0, problem.n_traces))
+        assert canon(allrows).shape[0] == allrows.shape[0], "a CM appears in two levels"
+        # every entry's reconstructed formula re-evaluates (by the oracle) to its CM
+        for k in range(1, depth + 1):
+            n = s.count(k)
+            for idx in sorted(set([0, n // 2, n - 1])) if n else []:
+                f = s.formula(k, idx)
+                cm = oracle_rows([spec.eval(f)], problem.word_bits, problem.n_traces)[0]
+                assert np.array_equal(cm, s.export(k, idx, 1)[0]), (k, idx, f)
+                from paper_2504_18943_gb300.workloads import formula_size
+                assert formula_size(f) == k, (k, f)
+    return run

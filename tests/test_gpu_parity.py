@@ -1,0 +1,281 @@
+"""CUDA path vs the CPU oracle, through the C ABI (needs a GB300).
+
+Bit-exact throughout: the same set of characteristic matrices per level, the
+same minimal size, and every returned formula separates the specification
+(checked by the oracle) with the reported size."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2504_18943_gb300 import workloads as W
+from tests.gpu_util import assert_levels_match, canon, lib, oracle_rows
+from tests.pins import GOLDEN
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    return lib()
+
+
+def _all_patterns(n_props, max_len):
+    """Traces over n_props propositions whose letters run through every pattern."""
+    traces = []
+    for length in range(1, max_len + 1):
+        for code in range(1 << (n_props * length)):
+            traces.append([[bool((code >> (t * n_props + p)) & 1) for p in range(n_props)]
+                           for t in range(length)])
+    T = len(traces)
+    bits = np.zeros((T, max_len, n_props), dtype=bool)
+    lengths = np.zeros(T, dtype=np.int32)
+    for i, tr in enumerate(traces):
+        lengths[i] = len(tr)
+        for t, letter in enumerate(tr):
+            bits[i, t] = letter
+    return W.TraceBatch(bits, lengths)
+
+
+def _eval_both(L, tb, n_props, formula, word_bits):
+    p = W.Problem("x", n_props, tb, len(tb), 0, word_bits)
+    got = L.lsyn_eval(L.pack_problem(p), formula)
+    want = oracle_rows([oracle.Spec.from_problem(p).eval(formula)], word_bits, len(tb))[0]
+    return got, want
+
+
+@pytest.mark.parametrize("word_bits", [32, 64])
+def test_eval_unary_exhaustive(L, word_bits):
+    tb = _all_patterns(1, 10)
+    for f in ["p0", "(! p0)", "(X p0)", "(F p0)", "(G p0)", "(X (X p0))", "(F (! p0))", "(G (X p0))",
+              "(! (G p0))", "(U p0 (X p0))"]:
+        got, want = _eval_both(L, tb, 1, f, word_bits)
+        assert np.array_equal(got, want), f
+
+
+@pytest.mark.parametrize("word_bits", [32, 64])
+def test_eval_binary_exhaustive(L, word_bits):
+    tb = _all_patterns(2, 5)
+    for f in ["(& p0 p1)", "(| p0 p1)", "(U p0 p1)", "(U p1 p0)", "(U (! p0) p1)", "(U p0 (X p1))",
+              "(G (| p0 p1))", "(F (& p0 (X p1)))"]:
+        got, want = _eval_both(L, tb, 2, f, word_bits)
+        assert np.array_equal(got, want), f
+
+
+@pytest.mark.parametrize("word_bits", [32, 64])
+def test_eval_full_width_traces(L, word_bits):
+    st = W.Stream(77)
+    tb = W.draw_traces(st, 300, 3, word_bits - 3, word_bits, np.full(3, 0.5))
+    fs = [W.random_formula(st, st.randint(1, 9), 3) for _ in range(60)]
+    fs += ["(F p0)", "(G p1)", "(U p0 p1)", "(X p2)", "(G (U p0 (! p1)))"]
+    for f in fs:
+        got, want = _eval_both(L, tb, 3, f, word_bits)
+        assert np.array_equal(got, want), f
+
+
+def test_eval_random_formulas(L):
+    for seed in range(4):
+        st = W.Stream(1000 + seed)
+        tb = W.draw_traces(st, 200, 4, 1, 20, np.full(4, 0.4))
+        for _ in range(50):
+            f = W.random_formula(st, st.randint(1, 12), 4)
+            got, want = _eval_both(L, tb, 4, f, 32)
+            assert np.array_equal(got, want), f
+
+
+def test_gpu_labelling_matches_oracle(L):
+    for seed in range(5):
+        a = W.tiny_problem(seed, L.labeller)
+        b = W.tiny_problem(seed, oracle.labeller)
+        assert a.hidden == b.hidden and np.array_equal(a.traces.bits, b.traces.bits)
+    a = W.mid_problem(0, L.labeller)
+    b = W.mid_problem(0, oracle.labeller)
+    assert np.array_equal(a.traces.bits, b.traces.bits) and np.array_equal(a.traces.lengths, b.traces.lengths)
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_levels_tiny(L, seed):
+    p = W.tiny_problem(seed, oracle.labeller)
+    assert_levels_match(L, p, 7)
+
+
+def test_solve_tiny_many(L):
+    for seed in range(100):
+        p = W.tiny_problem(seed, oracle.labeller)
+        spec = oracle.Spec.from_problem(p)
+        size, _, _ = spec.solve(8)
+        with L.Synthesizer(L.pack_problem(p), L.make_config(cache_bytes=64 << 20)) as s:
+            st, res, f, _ = s.solve(8)
+        assert st == L.LSYN_OK and res.found == 1 and res.exact == 1
+        assert res.size == size, (seed, res.size, size)
+        assert spec.separates(f) and W.formula_size(f) == size, (seed, f)
+
+
+def _golden_problem(name, word_bits=32):
+    g = GOLDEN[name]
+    return W.problem_from_strings(name, g["positive"], g["negative"], g["props"], word_bits)
+
+
+@pytest.mark.parametrize("mask", [oracle.PAPER_OPS, oracle.ALL_OPS])
+def test_paper_not_b_until_a(L, mask):
+    p = _golden_problem("not_b_until_a")
+    assert_levels_match(L, p, 6, op_mask=mask)
+    spec = oracle.Spec.from_problem(p)
+    size, _, _ = spec.solve(6, mask)
+    with L.Synthesizer(L.pack_problem(p), L.make_config(op_mask=mask, cache_bytes=64 << 20)) as s:
+        st, res, f, _ = s.solve(6)
+    assert st == L.LSYN_OK and res.size == size and spec.separates(f) and W.formula_size(f) == size
+    if mask == oracle.PAPER_OPS:
+        assert res.size == GOLDEN["not_b_until_a"]["min_size_paper_grammar"]
+
+
+@pytest.mark.parametrize("word_bits", [32, 64])
+def test_paper_size16_levels(L, word_bits):
+    p = _golden_problem("size16", word_bits)
+    assert_levels_match(L, p, 7, op_mask=oracle.PAPER_OPS)
+
+
+def test_paper_size16_solve(L):
+    """The paper's 14-trace example: with its grammar the minimal size is 16."""
+    g = GOLDEN["size16"]
+    p = _golden_problem("size16")
+    spec = oracle.Spec.from_problem(p)
+    with L.Synthesizer(L.pack_problem(p), L.make_config(op_mask=oracle.PAPER_OPS, cache_bytes=16 << 30)) as s:
+        st, res, f, levels = s.solve(16)
+    assert st == L.LSYN_OK, L.lsyn_last_error(s.ctx)
+    assert res.size == g["size"], res.size
+    assert spec.separates(f) and W.formula_size(f) == g["size"], f
+
+
+def test_mid_levels(L):
+    p = W.mid_problem(0, oracle.labeller)
+    assert_levels_match(L, p, 5, cache_bytes=1 << 30)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_mid_solve_full_size(L, seed):
+    """The mid-scale workload in the configuration the benchmark times (64 GiB
+    cache, early exit): minimal size, a valid formula, and sampled deep
+    entries re-evaluated one by one by the oracle."""
+    p = W.mid_problem(seed, oracle.labeller)
+    spec = oracle.Spec.from_problem(p)
+    packed = L.pack_problem(p)
+    with L.Synthesizer(packed, L.torch_config(cache_bytes=64 << 30)) as s:
+        st, res, f, levels = s.solve(16)
+        assert st == L.LSYN_OK, (st, L.lsyn_last_error(s.ctx))
+        assert spec.separates(f) and W.formula_size(f) == res.size
+        assert res.size <= W.formula_size(p.hidden)
+        # minimality against the oracle where it can reach
+        if res.size <= 5:
+            assert spec.solve(res.size)[0] == res.size
+        else:
+            assert spec.solve(5)[0] == 0
+        rng = np.random.default_rng(seed)
+        for k in range(1, res.size):
+            n = s.count(k)
+            rows = s.export(k, 0, min(n, 200000))
+            assert canon(rows).shape[0] == rows.shape[0], f"duplicates in level {k}"
+            for idx in rng.choice(n, size=min(n, 12), replace=False):
+                f_k = s.formula(k, int(idx))
+                cm = oracle_rows([spec.eval(f_k)], 32, p.n_traces)[0]
+                assert np.array_equal(cm, s.export(k, int(idx), 1)[0]) and W.formula_size(f_k) == k
+
+
+def _edge(name, pos, neg, props, word_bits=32):
+    return W.problem_from_strings(name, pos, neg, props, word_bits)
+
+
+def _random_problem(seed, n_props, n_pos, n_neg, lo, hi, word_bits, p=0.5):
+    st = W.Stream(W.stream_key(seed, 55))
+    tb = W.draw_traces(st, n_pos + n_neg, n_props, lo, hi, np.full(n_props, p))
+    return W.Problem("edge", n_props, tb, n_pos, n_neg, word_bits)
+
+
+EDGE = {
+    "one_trace_len1": (lambda: _edge("a", [["a"]], [], "a"), 5),
+    "one_negative": (lambda: _edge("a", [], [["a", "", "a"]], "a"), 6),
+    "all_positive": (lambda: _random_problem(1, 2, 6, 0, 1, 6, 32), 6),
+    "all_negative": (lambda: _random_problem(2, 2, 0, 6, 1, 6, 32), 6),
+    "single_prop": (lambda: _random_problem(3, 1, 4, 4, 1, 8, 32), 7),
+    "duplicate_props": (lambda: _edge("d", [["ab", "ab", ""], ["", "ab"]], [["ab"], ["", ""]], "ab"), 6),
+    "length_one_traces": (lambda: _random_problem(4, 3, 5, 5, 1, 1, 32), 6),
+    "full_width_32": (lambda: _random_problem(5, 2, 3, 3, 30, 32, 32), 5),
+    "full_width_64": (lambda: _random_problem(6, 2, 3, 3, 60, 64, 64), 5),
+    "ragged_37_u32_warp_path": (lambda: _random_problem(7, 3, 20, 17, 2, 12, 32), 5),
+    "ragged_129_u32_two_vectors_per_lane": (lambda: _random_problem(8, 2, 64, 65, 2, 10, 32), 5),
+    "ragged_100_u64": (lambda: _random_problem(9, 2, 50, 50, 30, 64, 64), 5),
+    "u64_300_traces_eight_vectors_per_lane": (lambda: _random_problem(10, 2, 150, 150, 5, 40, 64), 4),
+    "u64_small_thread_path": (lambda: _random_problem(11, 3, 3, 4, 40, 64, 64), 6),
+    "sixteen_traces_thread_path": (lambda: _random_problem(12, 2, 8, 8, 3, 12, 32), 6),
+}
+
+
+@pytest.mark.parametrize("name", sorted(EDGE))
+def test_edge_cases(L, name):
+    make, depth = EDGE[name]
+    assert_levels_match(L, make(), depth)
+
+
+def test_cache_full_path(L):
+    p = W.tiny_problem(5, oracle.labeller)
+    spec = oracle.Spec.from_problem(p)
+    run = spec.enumerate(8)
+    packed = L.pack_problem(p)
+    # room for a few hundred entries only
+    with L.Synthesizer(packed, L.make_config(cache_bytes=64 * 1024, full_levels=True)) as s:
+        full_at = None
+        for k in range(1, 9):
+            st = s.level(k)
+            if st.cache_full:
+                full_at = k
+                break
+            got = canon(s.export(k))
+            assert np.array_equal(got, canon(oracle_rows(run.cms(k), 32, p.n_traces)))
+        assert full_at is not None
+        with pytest.raises(L.LsynError) as ei:
+            s.level(full_at + 1)
+        assert ei.value.status == L.LSYN_E_STATE
+
+
+def test_solve_reports_cache_full(L):
+    g = GOLDEN["size16"]
+    p = W.problem_from_strings("e3", g["positive"], g["negative"], g["props"])
+    with L.Synthesizer(L.pack_problem(p), L.make_config(op_mask=oracle.PAPER_OPS, cache_bytes=1 << 20)) as s:
+        st, res, f, _ = s.solve(16)
+    assert st == L.LSYN_E_CACHE_FULL and res.found == 0 and f is None
+
+
+def test_reset_and_repeat(L):
+    p = W.mid_problem(1, oracle.labeller)
+    with L.Synthesizer(L.pack_problem(p), L.make_config(cache_bytes=4 << 30)) as s:
+        st1, r1, f1, _ = s.solve(12)
+        n1 = [s.count(k) for k in range(1, r1.size)]
+        s.reset()
+        st2, r2, f2, _ = s.solve(12)
+        n2 = [s.count(k) for k in range(1, r2.size)]
+    assert st1 == st2 == L.LSYN_OK and r1.size == r2.size and n1 == n2
+
+
+def test_full_levels_and_early_exit_agree(L):
+    for seed in range(10):
+        p = W.tiny_problem(100 + seed, oracle.labeller)
+        sizes = []
+        for full in (False, True):
+            with L.Synthesizer(L.pack_problem(p), L.make_config(full_levels=full, cache_bytes=64 << 20)) as s:
+                st, res, f, _ = s.solve(8)
+                sizes.append(res.size)
+        assert sizes[0] == sizes[1]
+
+
+def test_torch_allocator_and_stream(L):
+    import torch
+    p = W.tiny_problem(9, oracle.labeller)
+    stream = torch.cuda.Stream()
+    cfg = L.torch_config(full_levels=True, cache_bytes=64 << 20, stream=stream)
+    assert_levels_match(L, p, 6, config=cfg)
+
+
+def test_large_matrices_unsupported_yet(L):
+    p = _random_problem(13, 2, 300, 300, 4, 8, 64)  # 4800-byte matrices
+    with pytest.raises(L.LsynError) as ei:
+        L.Synthesizer(L.pack_problem(p))
+    assert ei.value.status == L.LSYN_E_UNSUPPORTED
