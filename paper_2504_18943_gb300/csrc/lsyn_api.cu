@@ -90,6 +90,12 @@ struct lsyn_ctx {
   uint4* atoms = nullptr;   // [n_props][vecs]
   unsigned long long* defer[2] = {nullptr, nullptr};
   unsigned defer_cap = 0;
+  unsigned* slotpos = nullptr;  // [max_entries]
+  uint2* holes = nullptr;       // [hole_cap]
+  unsigned hole_cap = 0;
+  uint2* moves = nullptr;       // [move_cap]
+  unsigned move_cap = 0;
+  unsigned chunk = 1;
   char* fbuf = nullptr;
   int* fstatus = nullptr;
   static constexpr unsigned kFormulaCap = 1u << 16;
@@ -133,6 +139,10 @@ struct lsyn_ctx {
     cv.defer_out = defer_out;
     cv.defer_out_n = defer_out_n;
     cv.defer_cap = defer_cap;
+    cv.slotpos = slotpos;
+    cv.holes = holes;
+    cv.hole_cap = hole_cap;
+    cv.chunk = chunk;
     cv.steps = steps;
     cv.early_exit = full_levels ? 0 : 1;
     return cv;
@@ -148,7 +158,9 @@ __global__ void k_level_begin(DevCounters* c) {
   c->defer_n[0] = 0;
   c->defer_n[1] = 0;
   c->defer_overflow = 0;
+  c->holes_n = 0;
   c->built = 0;
+  c->inserted = 0;
   for (int i = 0; i < 8; ++i) c->work[i] = 0;
   c->sol = ~0ull;
 }
@@ -433,7 +445,7 @@ lsyn_status lsyn_create(const lsyn_problem* problem, const lsyn_config* config, 
   unsigned long long best_cap = 0, best_e = 0;
   for (unsigned long long cap = 1024; cap <= (1ull << 34); cap <<= 1) {
     if (cap * 8 >= cache_bytes) break;
-    unsigned long long e = (cache_bytes - cap * 8) / (M + 8);
+    unsigned long long e = (cache_bytes - cap * 8) / (M + 12);
     e = std::min<unsigned long long>(e, (unsigned long long)(double(cap) * load));
     e = std::min<unsigned long long>(e, kMaxEntries);
     if (e > best_e) { best_e = e; best_cap = cap; }
@@ -461,6 +473,8 @@ lsyn_status lsyn_create(const lsyn_problem* problem, const lsyn_config* config, 
   c->table_cap = best_cap;
   c->max_entries = unsigned(best_e);
   c->defer_cap = 1u << 20;
+  c->hole_cap = 1u << 16;
+  c->move_cap = c->hole_cap * 32u;
 
   auto bail = [&](lsyn_status st, const std::string& msg) {
     g_create_error = msg;
@@ -484,10 +498,13 @@ lsyn_status lsyn_create(const lsyn_problem* problem, const lsyn_config* config, 
   c->atoms = static_cast<uint4*>(c->mem.get(size_t(c->n_props) * M));
   c->defer[0] = static_cast<unsigned long long*>(c->mem.get(size_t(c->defer_cap) * 8));
   c->defer[1] = static_cast<unsigned long long*>(c->mem.get(size_t(c->defer_cap) * 8));
+  c->slotpos = static_cast<unsigned*>(c->mem.get(size_t(c->max_entries) * 4));
+  c->holes = static_cast<uint2*>(c->mem.get(size_t(c->hole_cap) * sizeof(uint2)));
+  c->moves = static_cast<uint2*>(c->mem.get(size_t(c->move_cap) * sizeof(uint2)));
   c->fbuf = static_cast<char*>(c->mem.get(lsyn_ctx::kFormulaCap));
   c->fstatus = static_cast<int*>(c->mem.get(sizeof(int)));
   if (!c->arena || !c->prov || !c->table || !c->ctr || !c->consts || !c->atoms || !c->defer[0] || !c->defer[1] ||
-      !c->fbuf || !c->fstatus)
+      !c->fbuf || !c->fstatus || !c->slotpos || !c->holes || !c->moves)
     return bail(LSYN_E_NOMEM, "device allocation failed");
   if (cudaMallocHost(&c->h_snap, sizeof(Snap) * lsyn_ctx::kSnaps) != cudaSuccess ||
       cudaMallocHost(&c->h_fbuf, lsyn_ctx::kFormulaCap) != cudaSuccess ||
@@ -549,6 +566,14 @@ lsyn_status lsyn_enumerate_level(lsyn_ctx* c, int32_t k, lsyn_level_stats* out) 
   };
 
   const uint32_t start = c->level_start.back() + c->level_n.back();
+  // Ids a warp reserves at a time: large enough to keep the shared counter
+  // cold, small enough that the reservations of every resident warp stay a
+  // small part of the free arena.
+  {
+    const unsigned long long free_ids = c->max_entries > start ? c->max_entries - start : 0;
+    const unsigned long long warps = (unsigned long long)c->sms * 24ull;
+    c->chunk = unsigned(std::max(1ull, std::min(32ull, free_ids / (8ull * warps))));
+  }
   int launches = 0;
   ev_begin();
   k_level_begin<<<1, 1, 0, c->stream>>>(c->ctr);
@@ -590,7 +615,7 @@ lsyn_status lsyn_enumerate_level(lsyn_ctx* c, int32_t k, lsyn_level_stats* out) 
       memset(&plan, 0, sizeof(plan));
       plan.ops = bops;
       plan.work_slot = 0;
-      plan.tile = c->path == 2 ? std::max(1u, std::min(32u, unsigned((64 * 1024) / (c->vecs * 16)))) : 1u;
+      plan.tile = c->path == 2 ? std::max(1u, std::min(32u, unsigned((48 * 1024) / (c->vecs * 16)))) : 1u;
       unsigned long long tiles = 0, pairs = 0;
       for (int i = 1; 2 * i <= k - 1; ++i) {
         const int j = k - 1 - i;
@@ -656,9 +681,62 @@ lsyn_status lsyn_enumerate_level(lsyn_ctx* c, int32_t k, lsyn_level_stats* out) 
     cur = 1 - cur;
   }
   const DevCounters& h = c->h_snap[snap - 1].c;
-  if (h.error) return c->fail(LSYN_E_STATE, "hash table probe overflow");
-  const uint32_t total = std::min(h.n_entries, c->max_entries);
+  if (h.error) return c->fail(LSYN_E_STATE, "internal consistency check failed (code " + std::to_string(h.error) + ")");
+  uint32_t total = std::min(h.n_entries, c->max_entries);
+  if (h.holes_n) {
+    // Fill the id ranges warps reserved but left unused: move the entries
+    // above the level's dense end into them, so the level stays contiguous.
+    if (h.holes_n > c->hole_cap) return c->fail(LSYN_E_STATE, "hole log overflow");
+    std::vector<uint2> hr(h.holes_n);
+    e = cudaMemcpyAsync(hr.data(), c->holes, hr.size() * sizeof(uint2), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return c->cuda_fail(e, "hole log copy");
+    std::vector<std::pair<uint32_t, uint32_t>> rng;
+    for (const uint2& r : hr) {
+      const uint32_t lo = std::max(r.x, start), hi = std::min(r.y, total);
+      if (lo < hi) rng.push_back({lo, hi});
+    }
+    std::sort(rng.begin(), rng.end());
+    uint64_t H = 0;
+    for (auto& r : rng) H += r.second - r.first;
+    const uint32_t dense_end = total - uint32_t(H);
+    std::vector<uint2> mv;
+    size_t ri = 0;  // range holding or following the next valid candidate id >= dense_end
+    uint32_t v = dense_end;
+    auto next_valid = [&]() {
+      while (ri < rng.size() && rng[ri].second <= v) ++ri;
+      while (ri < rng.size() && rng[ri].first <= v && v < rng[ri].second) { v = rng[ri].second; ++ri; }
+    };
+    for (auto& r : rng) {
+      for (uint32_t hole = r.first; hole < r.second && hole < dense_end; ++hole) {
+        next_valid();
+        mv.push_back(make_uint2(v, hole));
+        ++v;
+      }
+    }
+    if (mv.size() > c->move_cap) return c->fail(LSYN_E_STATE, "too many hole moves");
+    if (!mv.empty()) {
+      e = cudaMemcpyAsync(c->moves, mv.data(), mv.size() * sizeof(uint2), cudaMemcpyHostToDevice, c->stream);
+      if (e != cudaSuccess) return c->cuda_fail(e, "moves copy");
+      ev_begin();
+      e = c->word_bits == 32 ? Kernels<uint32_t>::fixup(cv, c->moves, unsigned(mv.size()), lc)
+                             : Kernels<uint64_t>::fixup(cv, c->moves, unsigned(mv.size()), lc);
+      ++launches;
+      if (e != cudaSuccess) return c->cuda_fail(e, "fixup kernel");
+      ev_end(3);
+    }
+    const unsigned de = dense_end;
+    e = cudaMemcpyAsync(&c->ctr->n_entries, &de, sizeof(unsigned), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&c->ctr->holes_n, 0, sizeof(unsigned), c->stream);
+    if (e == cudaSuccess && (e = take_snap()) == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return c->cuda_fail(e, "fixup sync");
+    if (c->h_snap[snap - 1].c.error) return c->fail(LSYN_E_STATE, "hole fixup found an inconsistent slot");
+    total = dense_end;
+  }
   const uint32_t unique = total - start;
+  if (c->h_snap[snap - 1].c.inserted != unique)
+    return c->fail(LSYN_E_STATE, "insert count " + std::to_string(c->h_snap[snap - 1].c.inserted) +
+                                     " differs from the level size " + std::to_string(unique));
   c->level_start.push_back(start);
   c->level_n.push_back(unique);
   c->levels_done = k;
@@ -686,7 +764,7 @@ lsyn_status lsyn_enumerate_level(lsyn_ctx* c, int32_t k, lsyn_level_stats* out) 
       const DevCounters& b0 = c->h_snap[binary_snap - 1].c;
       const DevCounters& b1 = c->h_snap[binary_snap].c;
       const double Cb = double(b1.built - b0.built);
-      const double Ub = double(std::min(b1.n_entries, c->max_entries) - std::min(b0.n_entries, c->max_entries));
+      const double Ub = double(b1.inserted - b0.inserted);
       out->bytes_binary = op_bytes_binary + Cb * 32.0 + (Cb - Ub) * M + Ub * (M + 16.0);
     }
     if (c->timing) {

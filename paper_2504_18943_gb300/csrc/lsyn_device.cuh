@@ -111,6 +111,17 @@ __device__ __forceinline__ void h_acc(uint4 v, uint4 key, uint4 mul, uint32_t& l
   p = uint64_t(v.w ^ key.w) * mul.w; lo += uint32_t(p); hi += uint32_t(p >> 32);
 }
 
+// Warp-path variant of the hash: acc += w_i * mul_i (64-bit products and sum)
+// per 32-bit word, then the two 32-bit halves are summed across the warp and
+// finalised with h_fin. Equal CMs hash equally; that is all dedup needs.
+__device__ __forceinline__ uint64_t h_mac(uint4 v, uint4 mul, uint64_t acc) {
+  acc += uint64_t(v.x) * mul.x;
+  acc += uint64_t(v.y) * mul.y;
+  acc += uint64_t(v.z) * mul.z;
+  acc += uint64_t(v.w) * mul.w;
+  return acc;
+}
+
 __device__ __forceinline__ uint64_t h_fin(uint32_t hi, uint32_t lo) {
   uint64_t x = (uint64_t(hi) << 32) | lo;
   x ^= x >> 31;
@@ -131,12 +142,6 @@ __device__ __forceinline__ uint32_t spec_bad(uint4 c, uint4 lab, uint4 care) {
 
 __device__ __forceinline__ uint32_t v_ne(uint4 a, uint4 b) {
   return (a.x ^ b.x) | (a.y ^ b.y) | (a.z ^ b.z) | (a.w ^ b.w);
-}
-
-__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
 }
 
 __device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v) {
@@ -195,7 +200,7 @@ struct PathA {
   }
 
   // Spec check, then probe / compare / insert one candidate.
-  __device__ static void process(const CacheView& cv, const Consts& s, const uint4 (&c)[V], uint64_t desc) {
+  __device__ static unsigned process(const CacheView& cv, const Consts& s, const uint4 (&c)[V], uint64_t desc) {
     uint32_t lo = 0, hi = 0, bad = 0;
 #pragma unroll
     for (int v = 0; v < V; ++v) {
@@ -208,44 +213,43 @@ struct PathA {
     unsigned long long pos = h & cv.table_mask;
     for (unsigned long long it = 0; it <= cv.table_mask; ++it, pos = (pos + 1) & cv.table_mask) {
       unsigned long long* slot = cv.table + pos;
-      unsigned long long sv = ld_acquire(slot);
+      // One atomic per probe: claims an empty slot, or returns what is there.
+      const unsigned long long sv = atomicCAS(slot, 0ull, tag | kSlotPending);
       if (sv == 0ull) {
-        sv = atomicCAS(slot, 0ull, tag | kSlotPending);
-        if (sv == 0ull) {
-          const unsigned id = atomicAdd(&cv.ctr->n_entries, 1u);
-          if (id >= cv.max_entries) {
-            st_release(slot, tag | kSlotTomb);
-            atomicExch(&cv.ctr->full, 1u);
-            return;
-          }
-          uint4* dst = cv.arena + size_t(id) * cv.vecs;
-#pragma unroll
-          for (int v = 0; v < V; ++v) dst[v] = c[v];
-          cv.prov[id] = desc;
-          __threadfence();
-          st_release(slot, tag | (unsigned long long)(id + 1u));
-          return;
+        const unsigned id = atomicAdd(&cv.ctr->n_entries, 1u);
+        if (id >= cv.max_entries) {
+          st_release(slot, tag | kSlotTomb);
+          atomicExch(&cv.ctr->full, 1u);
+          return 0;
         }
+        uint4* dst = cv.arena + size_t(id) * cv.vecs;
+#pragma unroll
+        for (int v = 0; v < V; ++v) dst[v] = c[v];
+        cv.prov[id] = desc;
+        cv.slotpos[id] = unsigned(pos);
+        st_release(slot, tag | (unsigned long long)(id + 1u));  // orders this thread's CM and provenance first
+        return 1;
       }
       if ((sv & 0xFFFFFFFF00000000ull) != tag) continue;
       const uint32_t low = uint32_t(sv);
-      if (low == kSlotPending) { defer(cv, desc); return; }
+      if (low == kSlotPending) { defer(cv, desc); return 0; }
       if (low == kSlotTomb) continue;
       const uint4* src = row_ptr(cv, low - 1u);
       uint32_t ne = 0;
 #pragma unroll
       for (int v = 0; v < V; ++v) ne |= v_ne(__ldcg(src + v), c[v]);
-      if (ne == 0) return;  // duplicate: an equal CM is already cached
+      if (ne == 0) return 0;  // duplicate: an equal CM is already cached
     }
     atomicExch(&cv.ctr->error, 1u);
+    return 0;
   }
 
-  __device__ static void candidate(const CacheView& cv, const Consts& s, uint32_t op, const uint4 (&a)[V],
-                                   const uint4 (&b)[V], uint64_t desc) {
+  __device__ static unsigned candidate(const CacheView& cv, const Consts& s, uint32_t op, const uint4 (&a)[V],
+                                       const uint4 (&b)[V], uint64_t desc) {
     uint4 c[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) c[v] = v_op<W>(op, a[v], b[v], s.lm[v], cv.steps);
-    process(cv, s, c, desc);
+    return process(cv, s, c, desc);
   }
 };
 
@@ -255,7 +259,7 @@ __global__ void __launch_bounds__(256) k_unary_a(CacheView cv, uint32_t first, u
   __shared__ typename P::Consts s;
   P::load_consts(cv, &s);
   __syncthreads();
-  unsigned long long built = 0;
+  unsigned long long built = 0, ins = 0;
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
     if (stop_requested(cv)) break;
@@ -266,11 +270,12 @@ __global__ void __launch_bounds__(256) k_unary_a(CacheView cv, uint32_t first, u
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       if (!((ops >> q) & 1u)) continue;
-      P::candidate(cv, s, opc[q], a, a, pack_desc(opc[q], id, 0));
+      ins += P::candidate(cv, s, opc[q], a, a, pack_desc(opc[q], id, 0));
       ++built;
     }
   }
   if (built) atomicAdd(&cv.ctr->built, built);
+  if (ins) atomicAdd(&cv.ctr->inserted, ins);
 }
 
 template <typename W, int V>
@@ -279,7 +284,7 @@ __global__ void __launch_bounds__(256) k_binary_a(CacheView cv, BinaryPlan plan)
   __shared__ typename P::Consts s;
   P::load_consts(cv, &s);
   __syncthreads();
-  unsigned long long built = 0;
+  unsigned long long built = 0, ins = 0;
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
   for (unsigned long long p = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; p < plan.total_pairs;
        p += stride) {
@@ -295,12 +300,13 @@ __global__ void __launch_bounds__(256) k_binary_a(CacheView cv, BinaryPlan plan)
     uint4 a[V], b[V];
     P::load_row(row_ptr(cv, a_id), a);
     P::load_row(row_ptr(cv, b_id), b);
-    if (plan.ops & 1u) { P::candidate(cv, s, kAnd, a, b, pack_desc(kAnd, a_id, b_id)); ++built; }
-    if (plan.ops & 2u) { P::candidate(cv, s, kOr, a, b, pack_desc(kOr, a_id, b_id)); ++built; }
-    if (plan.ops & 4u) { P::candidate(cv, s, kUntil, a, b, pack_desc(kUntil, a_id, b_id)); ++built; }
-    if (plan.ops & 8u) { P::candidate(cv, s, kUntil, b, a, pack_desc(kUntil, b_id, a_id)); ++built; }
+    if (plan.ops & 1u) { ins += P::candidate(cv, s, kAnd, a, b, pack_desc(kAnd, a_id, b_id)); ++built; }
+    if (plan.ops & 2u) { ins += P::candidate(cv, s, kOr, a, b, pack_desc(kOr, a_id, b_id)); ++built; }
+    if (plan.ops & 4u) { ins += P::candidate(cv, s, kUntil, a, b, pack_desc(kUntil, a_id, b_id)); ++built; }
+    if (plan.ops & 8u) { ins += P::candidate(cv, s, kUntil, b, a, pack_desc(kUntil, b_id, a_id)); ++built; }
   }
   if (built) atomicAdd(&cv.ctr->built, built);
+  if (ins) atomicAdd(&cv.ctr->inserted, ins);
 }
 
 // Rebuild a candidate from its descriptor (operands are complete levels).
@@ -333,37 +339,69 @@ __global__ void __launch_bounds__(256) k_desc_a(CacheView cv, const unsigned lon
   unsigned n = implicit_atoms;
   if (list) n = min(*list_n, list_cap);
   const uint32_t stride = gridDim.x * blockDim.x;
+  unsigned long long ins = 0;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     if (stop_requested(cv)) break;
     const uint64_t d = list ? list[i] : pack_desc(kAtom, i, 0);
     uint4 c[V];
     rebuild_a<W, V>(cv, s, d, c);
-    P::process(cv, s, c, d);
+    ins += P::process(cv, s, c, d);
   }
+  if (ins) atomicAdd(&cv.ctr->inserted, ins);
   if (implicit_atoms && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&cv.ctr->built, (unsigned long long)n);
 }
 
 // ===========================================================================
 // Path B: a warp holds a CM; lane l holds vectors l, l + 32, ... (RV of them).
-// Candidates are processed in batches of up to NB so that their table probes
-// and compare reads are in flight together.
+// Candidates go through the dedup in batches of NB = 8 / RV, so that their
+// table probes (one CAS per probe, issued by lane q for candidate q) and their
+// compare reads are in flight together. Compare reads are staged into shared
+// memory with cp.async (L2-coherent, no registers held while in flight); a
+// batch's new CMs are written, fenced once, and published.
 // ===========================================================================
+__device__ __forceinline__ void cp_async16(uint4* smem, const uint4* gmem) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
+__device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t comp(const uint4& v, int i) {
+  return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
+}
+
+// Bit 0 of every trace word of a vector, packed (word j -> bit j).
+template <typename W> __device__ __forceinline__ uint32_t bit0s(uint4 c);
+template <> __device__ __forceinline__ uint32_t bit0s<uint32_t>(uint4 c) {
+  return (c.x & 1u) | ((c.y & 1u) << 1) | ((c.z & 1u) << 2) | ((c.w & 1u) << 3);
+}
+template <> __device__ __forceinline__ uint32_t bit0s<uint64_t>(uint4 c) { return (c.x & 1u) | ((c.z & 1u) << 1); }
+
 template <typename W, int RV>
 struct PathB {
+  static constexpr int NB = 8 / RV;                  // candidates per batch
+  static constexpr int WPV = int(16 / sizeof(W));    // trace words per vector
+  static constexpr int kStage = NB * RV * 32;        // uint4 of compare staging per warp
+
   struct LaneConsts {
-    uint4 lm[RV], lab[RV], care[RV], key[RV], mul[RV];
+    uint4 mul[RV];  // hash multipliers of this lane's 32-bit words
+    uint32_t lab;   // bit (r * WPV + j): 1 iff word j of vector r belongs to a positive trace
   };
 
   __device__ static void load_consts(const CacheView& cv, LaneConsts& k) {
     const int lane = threadIdx.x & 31;
+    k.lab = 0;
 #pragma unroll
     for (int r = 0; r < RV; ++r) {
       const int v = lane + 32 * r;
-      k.lm[r] = cv.lenmask[v];
-      k.lab[r] = cv.label[v];
-      k.care[r] = cv.care[v];
-      k.key[r] = cv.hkey[v];
       k.mul[r] = cv.hmul[v];
+      k.lab |= bit0s<W>(cv.label[v]) << (r * WPV);
     }
   }
 
@@ -375,153 +413,243 @@ struct PathB {
 
   enum { kProbing = 0, kDone = 1, kClaimed = 2, kDeferred = 3 };
 
-  // Spec check, probe, compare and insert a batch of NB candidates; bit q of
-  // `en` says candidate q is real. c and desc are warp-uniform in meaning.
-  template <int NB>
-  __device__ static void batch(const CacheView& cv, const LaneConsts& k, const uint4 (&c)[NB][RV],
-                               const uint64_t (&desc)[NB], uint32_t en) {
+  // Ids this warp reserved from the shared counter and has not used yet:
+  // [next, end). Reserving `chunk` ids per counter update keeps the counter
+  // off the critical path; what a warp leaves unused when it exits is logged
+  // as a hole and filled after the level (Kernels::fixup).
+  struct Ids {
+    unsigned next = 0, end = 0;
+    unsigned long long inserted = 0;
+  };
+
+  __device__ static void retire(const CacheView& cv, Ids& ids) {
     const int lane = threadIdx.x & 31;
-    int my_state = kDone;
-    unsigned long long my_tag = 0, my_pos = 0;
-    uint64_t my_desc = 0;
-    uint32_t sol_mask = 0;
+    if (lane == 0) {
+      if (ids.next < ids.end && ids.next < cv.max_entries) {
+        const unsigned h = atomicAdd(&cv.ctr->holes_n, 1u);
+        if (h < cv.hole_cap) cv.holes[h] = make_uint2(ids.next, min(ids.end, cv.max_entries));
+        else atomicExch(&cv.ctr->error, 2u);
+      }
+      if (ids.inserted) atomicAdd(&cv.ctr->inserted, ids.inserted);
+    }
+    ids.next = ids.end = 0;
+    ids.inserted = 0;
+  }
+
+  // A slot this lane claimed whose CM words were stored but not yet
+  // published. It is published by the next batch (or by flush()), after a
+  // fence that by then no longer waits for those stores: the fence is off the
+  // critical path. Meanwhile the slot reads as pending and an equal candidate
+  // is deferred.
+  struct Pending {
+    unsigned long long* slot = nullptr;
+    unsigned long long val = 0;
+  };
+
+  // Publish this warp's pending slots (all lanes call it together).
+  __device__ static void flush(Pending& pend) {
+    if (__any_sync(kFull, pend.slot != nullptr)) {
+      fence_acq_rel_gpu();  // every lane: its stored CM words and provenance first
+      __syncwarp();
+      if (pend.slot) st_relaxed(pend.slot, pend.val);
+      pend.slot = nullptr;
+    }
+  }
+
+  // Spec check, probe, compare and insert a batch of NB candidates. Every lane
+  // holds its slices c[q][*] of every candidate q; lane q (q < NB) also holds
+  // the descriptor of candidate q. Bit q of `en` (warp-uniform) says candidate
+  // q is real. `stage` is this warp's kStage uint4 of shared memory.
+  __device__ static void batch(const CacheView& cv, const LaneConsts& k, const uint4 (&c)[NB][RV],
+                               uint64_t my_desc, uint32_t en, uint4* stage, Pending& pend, Ids& ids) {
+    const int lane = threadIdx.x & 31;
+    uint32_t my_lo = 0, my_hi = 0, bad = 0;
 #pragma unroll
     for (int q = 0; q < NB; ++q) {
-      if (!((en >> q) & 1u)) continue;
-      uint32_t lo = 0, hi = 0, bad = 0;
+      uint64_t acc = 0;
+      uint32_t bits = 0;
 #pragma unroll
       for (int r = 0; r < RV; ++r) {
-        h_acc(c[q][r], k.key[r], k.mul[r], lo, hi);
-        bad |= spec_bad(c[q][r], k.lab[r], k.care[r]);
+        acc = h_mac(c[q][r], k.mul[r], acc);
+        bits |= bit0s<W>(c[q][r]) << (r * WPV);
       }
-      lo = __reduce_add_sync(kFull, lo);
-      hi = __reduce_add_sync(kFull, hi);
-      if (!__any_sync(kFull, bad != 0)) sol_mask |= 1u << q;
-      if (lane == q) {
-        const uint64_t h = h_fin(hi, lo);
-        my_tag = (h >> 32) << 32;
-        my_pos = h & cv.table_mask;
-        my_state = kProbing;
-        my_desc = desc[q];
-      }
+      const uint32_t lo = __reduce_add_sync(kFull, uint32_t(acc));
+      const uint32_t hi = __reduce_add_sync(kFull, uint32_t(acc >> 32));
+      my_lo = lane == q ? lo : my_lo;
+      my_hi = lane == q ? hi : my_hi;
+      bad |= ((bits ^ k.lab) != 0u ? 1u : 0u) << q;
     }
-    if (sol_mask && lane < NB && ((sol_mask >> lane) & 1u)) record_solution(cv, my_desc);
+    // Separation (section "Synthesising ... from examples"): bit 0 of every
+    // trace word equals the trace's label. Padding words are 0 with label 0.
+    bad = __reduce_or_sync(kFull, bad);
+    const bool mine = lane < NB && ((en >> lane) & 1u);
+    if (mine && !((bad >> lane) & 1u)) record_solution(cv, my_desc);
 
-    uint32_t my_cmp = 0;
+    int state = mine ? kProbing : kDone;
+    const uint64_t h = h_fin(my_hi, my_lo);
+    const unsigned long long tag = (h >> 32) << 32;
+    unsigned long long pos = h & cv.table_mask;
+    uint32_t cmp_id = 0;
     unsigned long long guard = 0;
     while (true) {
-      bool need_cmp = false;
-      if (my_state == kProbing) {
-        unsigned long long* slot = cv.table + my_pos;
-        unsigned long long sv = ld_acquire(slot);
+      bool need = false;
+      if (state == kProbing) {
+        // One atomic per probe: claims an empty slot, or returns what is there.
+        const unsigned long long sv = atomicCAS(cv.table + pos, 0ull, tag | kSlotPending);
         if (sv == 0ull) {
-          sv = atomicCAS(slot, 0ull, my_tag | kSlotPending);
-          if (sv == 0ull) my_state = kClaimed;
-        }
-        if (my_state == kProbing) {
+          state = kClaimed;
+        } else {
           const uint32_t low = uint32_t(sv);
-          if ((sv & 0xFFFFFFFF00000000ull) != my_tag || low == kSlotTomb) {
-            my_pos = (my_pos + 1) & cv.table_mask;
-          } else if (low == kSlotPending) {
-            my_state = kDeferred;
-          } else {
-            need_cmp = true;
-            my_cmp = low - 1u;
+          if ((sv & 0xFFFFFFFF00000000ull) != tag || low == kSlotTomb) pos = (pos + 1) & cv.table_mask;
+          else if (low == kSlotPending) state = kDeferred;
+          else {
+            need = true;
+            cmp_id = low - 1u;
           }
         }
       }
-      const uint32_t cmp_mask = __ballot_sync(kFull, need_cmp);
-      if (cmp_mask) {
-        uint4 st[NB][RV];
+      const uint32_t cm = __ballot_sync(kFull, need);
+      if (cm) {
+        // The published entry's CM was made visible in L2 before its slot
+        // (writer's fence); cp.async.cg reads it from L2.
 #pragma unroll
         for (int q = 0; q < NB; ++q) {
-          const uint32_t id = __shfl_sync(kFull, my_cmp, q);
-          if ((cmp_mask >> q) & 1u) {
+          const uint32_t id = __shfl_sync(kFull, cmp_id, q);
+          if ((cm >> q) & 1u) {
             const uint4* src = row_ptr(cv, id);
 #pragma unroll
-            for (int r = 0; r < RV; ++r) st[q][r] = __ldcg(src + lane + 32 * r);
+            for (int r = 0; r < RV; ++r) cp_async16(stage + (q * RV + r) * 32 + lane, src + lane + 32 * r);
           }
         }
+        cp_async_wait_all();
+        uint32_t ne = 0;
 #pragma unroll
         for (int q = 0; q < NB; ++q) {
-          if (!((cmp_mask >> q) & 1u)) continue;
-          uint32_t ne = 0;
+          uint32_t d = 0;
+          if ((cm >> q) & 1u) {
 #pragma unroll
-          for (int r = 0; r < RV; ++r) ne |= v_ne(st[q][r], c[q][r]);
-          const bool eq = !__any_sync(kFull, ne != 0);
-          if (lane == q) {
-            if (eq) my_state = kDone;
-            else my_pos = (my_pos + 1) & cv.table_mask;
+            for (int r = 0; r < RV; ++r) d |= v_ne(stage[(q * RV + r) * 32 + lane], c[q][r]);
           }
+          ne |= (d != 0u ? 1u : 0u) << q;
+        }
+        ne = __reduce_or_sync(kFull, ne);
+        if (need) {
+          if (!((ne >> lane) & 1u)) state = kDone;  // equal CM already cached
+          else pos = (pos + 1) & cv.table_mask;
         }
       }
-      if (!__any_sync(kFull, my_state == kProbing)) break;
-      if (++guard > cv.table_mask + 1) {  // every slot seen: cannot happen at load <= 0.9
+      if (!__any_sync(kFull, state == kProbing)) break;
+      if (++guard > cv.table_mask) {  // every slot seen: cannot happen at load <= 0.9
         if (lane == 0) atomicExch(&cv.ctr->error, 1u);
-        if (my_state == kProbing) my_state = kDone;
+        if (state == kProbing) state = kDone;
       }
     }
 
-    const uint32_t claim = __ballot_sync(kFull, my_state == kClaimed);
+    const uint32_t claim = __ballot_sync(kFull, state == kClaimed);
+    const unsigned n_claim = unsigned(__popc(claim));
+    const unsigned have = ids.end - ids.next;  // warp-uniform
+    unsigned base = 0;
+    if (n_claim > have && lane == 0) base = atomicAdd(&cv.ctr->n_entries, max(cv.chunk, n_claim - have));
+    flush(pend);  // the previous batch's slots; overlaps the id reservation above
     if (claim) {
-      unsigned base = 0;
-      if (lane == 0) base = atomicAdd(&cv.ctr->n_entries, (unsigned)__popc(claim));
-      base = __shfl_sync(kFull, base, 0);
+      // Ids of the claimed candidates in lane order: first what is left of the
+      // current reservation, then a fresh one.
+      unsigned fresh = 0;
+      if (n_claim > have) {
+        fresh = __shfl_sync(kFull, base, 0);
+      }
+      auto id_of = [&](unsigned rank) { return rank < have ? ids.next + rank : fresh + (rank - have); };
 #pragma unroll
       for (int q = 0; q < NB; ++q) {
         if (!((claim >> q) & 1u)) continue;
-        const unsigned id = base + __popc(claim & ((1u << q) - 1u));
+        const unsigned id = id_of(unsigned(__popc(claim & ((1u << q) - 1u))));
         if (id < cv.max_entries) {
           uint4* dst = cv.arena + size_t(id) * cv.vecs;
 #pragma unroll
           for (int r = 0; r < RV; ++r) dst[lane + 32 * r] = c[q][r];
-          if (lane == 0) cv.prov[id] = desc[q];
         }
       }
-      __threadfence();
-      __syncwarp();
-      if (my_state == kClaimed) {
-        const unsigned id = base + __popc(claim & ((1u << lane) - 1u));
-        unsigned long long* slot = cv.table + my_pos;
-        if (id < cv.max_entries) {
-          st_release(slot, my_tag | (unsigned long long)(id + 1u));
+      const unsigned my_id = id_of(unsigned(__popc(claim & ((1u << lane) - 1u))));
+      if (n_claim > have) {
+        ids.next = fresh + (n_claim - have);
+        ids.end = fresh + max(cv.chunk, n_claim - have);
+      } else {
+        ids.next += n_claim;
+      }
+      ids.inserted += n_claim;
+      if (state == kClaimed) {
+        unsigned long long* slot = cv.table + pos;
+        if (my_id < cv.max_entries) {
+          cv.prov[my_id] = my_desc;
+          cv.slotpos[my_id] = unsigned(pos);
+          pend.slot = slot;
+          pend.val = tag | (unsigned long long)(my_id + 1u);
         } else {
-          st_release(slot, my_tag | kSlotTomb);
+          st_relaxed(slot, tag | kSlotTomb);  // nothing to order: no CM behind it
           atomicExch(&cv.ctr->full, 1u);
         }
       }
     }
-    if (my_state == kDeferred) defer(cv, my_desc);
+    if (state == kDeferred) defer(cv, my_desc);
   }
 };
 
+// Unary operator code of position o in the batch order (not, X, F, G).
+__device__ __forceinline__ uint32_t unary_code(int o) { return o == 0 ? kNot : uint32_t(3 + o); }
+
 template <typename W, int RV>
-__global__ void __launch_bounds__(256) k_unary_b(CacheView cv, uint32_t first, uint32_t count, uint32_t ops) {
+__global__ void __launch_bounds__(256, 3) k_unary_b(CacheView cv, uint32_t first, uint32_t count, uint32_t ops) {
   using P = PathB<W, RV>;
+  constexpr int NB = P::NB;
+  constexpr int ROWS = NB >= 4 ? NB / 4 : 1;  // rows per batch group
+  constexpr int G = NB >= 4 ? 1 : 4 / NB;     // batches per row group
+  extern __shared__ uint4 smem[];
+  const int lane = threadIdx.x & 31;
+  uint4* stage = smem + (threadIdx.x >> 5) * P::kStage;
   typename P::LaneConsts k;
   P::load_consts(cv, k);
-  const int lane = threadIdx.x & 31;
+  uint4 lm[RV];
+#pragma unroll
+  for (int r = 0; r < RV; ++r) lm[r] = cv.lenmask[lane + 32 * r];
   const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   unsigned long long built = 0;
-  for (uint32_t i = warp; i < count; i += nwarps) {
-    if (__any_sync(kFull, stop_requested(cv))) break;
-    const uint32_t id = first + i;
-    uint4 a[RV];
-    P::load_row(row_ptr(cv, id), a);
-    uint4 c[4][RV];
+  typename P::Pending pend;
+  typename P::Ids idr;
+  uint32_t iter = 0;
+  for (uint32_t base = warp * ROWS; base < count; base += nwarps * ROWS, ++iter) {
+    if ((iter & 3u) == 0 && __any_sync(kFull, stop_requested(cv))) break;
+    uint4 a[ROWS][RV];
+    uint32_t rows_ok = 0;
 #pragma unroll
-    for (int r = 0; r < RV; ++r) {
-      c[0][r] = v_op<W>(kNot, a[r], a[r], k.lm[r], cv.steps);
-      c[1][r] = v_op<W>(kNext, a[r], a[r], k.lm[r], cv.steps);
-      c[2][r] = v_op<W>(kFuture, a[r], a[r], k.lm[r], cv.steps);
-      c[3][r] = v_op<W>(kGlobally, a[r], a[r], k.lm[r], cv.steps);
+    for (int p = 0; p < ROWS; ++p) {
+      if (base + p < count) {
+        P::load_row(row_ptr(cv, first + base + p), a[p]);
+        rows_ok |= 1u << p;
+      } else {
+#pragma unroll
+        for (int r = 0; r < RV; ++r) a[p][r] = make_uint4(0, 0, 0, 0);
+      }
     }
-    const uint64_t d[4] = {pack_desc(kNot, id, 0), pack_desc(kNext, id, 0), pack_desc(kFuture, id, 0),
-                           pack_desc(kGlobally, id, 0)};
-    P::template batch<4>(cv, k, c, d, ops & 0xFu);
-    built += __popc(ops & 0xFu);
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      uint4 c[NB][RV];
+      uint32_t en = 0;
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        const int flat = g * NB + j, p = flat / 4, o = flat % 4;
+#pragma unroll
+        for (int r = 0; r < RV; ++r) c[j][r] = v_op<W>(unary_code(o), a[p][r], a[p][r], lm[r], cv.steps);
+        if (((rows_ok >> p) & 1u) && ((ops >> o) & 1u)) en |= 1u << j;
+      }
+      const int flat = g * NB + lane;
+      const uint64_t my_desc = pack_desc(unary_code(flat & 3), first + base + uint32_t(flat >> 2), 0);
+      P::batch(cv, k, c, my_desc, en, stage, pend, idr);
+      built += __popc(en);
+    }
   }
+  P::flush(pend);
+  P::retire(cv, idr);
   if (lane == 0 && built) atomicAdd(&cv.ctr->built, built);
 }
 
@@ -531,17 +659,25 @@ __global__ void __launch_bounds__(256) k_unary_b(CacheView cv, uint32_t first, u
 // streams rows of the other level through registers, building a & b, a | b,
 // a U b and b U a for every staged row a.
 template <typename W, int RV>
-__global__ void __launch_bounds__(256) k_binary_b(CacheView cv, BinaryPlan plan) {
+__global__ void __launch_bounds__(256, 3) k_binary_b(CacheView cv, BinaryPlan plan) {
   using P = PathB<W, RV>;
-  extern __shared__ uint4 s_left[];
+  constexpr int NB = P::NB;
+  constexpr int PAIRS = NB >= 4 ? NB / 4 : 1;  // pairs per batch group
+  constexpr int G = NB >= 4 ? 1 : 4 / NB;      // batches per pair group
+  extern __shared__ uint4 smem[];
   __shared__ unsigned long long s_tile;
-  typename P::LaneConsts k;
-  P::load_consts(cv, k);
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
   const unsigned vecs = cv.vecs;
+  uint4* s_left = smem;
+  uint4* stage = smem + size_t(plan.tile) * vecs + warp * P::kStage;
+  typename P::LaneConsts k;
+  P::load_consts(cv, k);
+  const uint4 zero = make_uint4(0, 0, 0, 0);
   unsigned long long built = 0;
+  typename P::Pending pend;
+  typename P::Ids idr;
   while (true) {
     if (threadIdx.x == 0) {
       unsigned long long t = atomicAdd(&cv.ctr->work[plan.work_slot], 1ull);
@@ -572,66 +708,131 @@ __global__ void __launch_bounds__(256) k_binary_b(CacheView cv, BinaryPlan plan)
       const uint32_t b_id = S.right_start + r0 + rr;
       uint4 b[RV];
       P::load_row(row_ptr(cv, b_id), b);
-      for (uint32_t li = 0; li < ln; ++li) {
-        const uint32_t a_id = S.left_start + l0 + li;
-        if (S.tri && a_id >= b_id) break;  // same level: pairs a < b only (rows ascend)
-        uint4 a[RV];
+      for (uint32_t li = 0; li < ln; li += PAIRS) {
+        uint4 a[PAIRS][RV];
+        const uint32_t a0 = S.left_start + l0 + li;
+        uint32_t pv = 0;
 #pragma unroll
-        for (int r = 0; r < RV; ++r) a[r] = s_left[li * vecs + lane + 32 * r];
-        uint4 c[4][RV];
+        for (int p = 0; p < PAIRS; ++p) {
+          const bool ok = li + p < ln && (!S.tri || a0 + p < b_id);
+          if (ok) pv |= 1u << p;
 #pragma unroll
-        for (int r = 0; r < RV; ++r) {
-          c[0][r] = v_op<W>(kAnd, a[r], b[r], k.lm[r], cv.steps);
-          c[1][r] = v_op<W>(kOr, a[r], b[r], k.lm[r], cv.steps);
-          c[2][r] = v_op<W>(kUntil, a[r], b[r], k.lm[r], cv.steps);
-          c[3][r] = v_op<W>(kUntil, b[r], a[r], k.lm[r], cv.steps);
+          for (int r = 0; r < RV; ++r) a[p][r] = ok ? s_left[(li + p) * vecs + lane + 32 * r] : zero;
         }
-        const uint64_t d[4] = {pack_desc(kAnd, a_id, b_id), pack_desc(kOr, a_id, b_id),
-                               pack_desc(kUntil, a_id, b_id), pack_desc(kUntil, b_id, a_id)};
-        P::template batch<4>(cv, k, c, d, plan.ops);
-        built += __popc(plan.ops);
+        if (!pv) break;  // rows ascend: no later row pairs with b either
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+          uint4 c[NB][RV];
+          uint32_t en = 0;
+#pragma unroll
+          for (int j = 0; j < NB; ++j) {
+            const int flat = g * NB + j, p = flat / 4, o = flat % 4;
+#pragma unroll
+            for (int r = 0; r < RV; ++r) {
+              if (o == 0) c[j][r] = v_op<W>(kAnd, a[p][r], b[r], b[r], cv.steps);
+              else if (o == 1) c[j][r] = v_op<W>(kOr, a[p][r], b[r], b[r], cv.steps);
+              else if (o == 2) c[j][r] = v_op<W>(kUntil, a[p][r], b[r], b[r], cv.steps);
+              else c[j][r] = v_op<W>(kUntil, b[r], a[p][r], b[r], cv.steps);
+            }
+            if (((pv >> p) & 1u) && ((plan.ops >> o) & 1u)) en |= 1u << j;
+          }
+          // lane q's candidate: pair q / 4 of the group, operator q % 4
+          const int flat = g * NB + lane, o = flat & 3;
+          const uint32_t ai = a0 + uint32_t(flat >> 2);
+          const uint64_t my_desc = o == 0 ? pack_desc(kAnd, ai, b_id)
+                                 : o == 1 ? pack_desc(kOr, ai, b_id)
+                                 : o == 2 ? pack_desc(kUntil, ai, b_id)
+                                          : pack_desc(kUntil, b_id, ai);
+          P::batch(cv, k, c, my_desc, en, stage, pend, idr);
+          built += __popc(en);
+        }
       }
     }
     __syncthreads();
   }
+  P::flush(pend);
+  P::retire(cv, idr);
   if (lane == 0 && built) atomicAdd(&cv.ctr->built, built);
 }
 
 template <typename W, int RV>
-__global__ void __launch_bounds__(256) k_desc_b(CacheView cv, const unsigned long long* list,
-                                                const unsigned int* list_n, unsigned int list_cap,
-                                                unsigned int implicit_atoms) {
+__global__ void __launch_bounds__(256, 3) k_desc_b(CacheView cv, const unsigned long long* list,
+                                                   const unsigned int* list_n, unsigned int list_cap,
+                                                   unsigned int implicit_atoms) {
   using P = PathB<W, RV>;
+  constexpr int NB = P::NB;
+  extern __shared__ uint4 smem[];
+  const int lane = threadIdx.x & 31;
+  uint4* stage = smem + (threadIdx.x >> 5) * P::kStage;
   typename P::LaneConsts k;
   P::load_consts(cv, k);
-  const int lane = threadIdx.x & 31;
+  uint4 lm[RV];
+#pragma unroll
+  for (int r = 0; r < RV; ++r) lm[r] = cv.lenmask[lane + 32 * r];
   const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   unsigned n = implicit_atoms;
   if (list) n = min(*list_n, list_cap);
-  for (uint32_t i = warp; i < n; i += nwarps) {
+  typename P::Pending pend;
+  typename P::Ids idr;
+  for (uint32_t base = warp * NB; base < n; base += nwarps * NB) {
     if (__any_sync(kFull, stop_requested(cv))) break;
-    const uint64_t d = list ? list[i] : pack_desc(kAtom, i, 0);
-    const uint32_t op = desc_op(d);
-    uint4 c[1][RV];
-    if (op == kAtom) {
-      P::load_row(cv.atoms + size_t(desc_left(d)) * cv.vecs, c[0]);
-    } else {
-      uint4 a[RV], b[RV];
-      P::load_row(row_ptr(cv, desc_left(d)), a);
-      if (op == kAnd || op == kOr || op == kUntil) P::load_row(row_ptr(cv, desc_right(d)), b);
-      else {
+    uint4 c[NB][RV];
+    uint32_t en = 0;
+    uint64_t my_desc = 0;
 #pragma unroll
-        for (int r = 0; r < RV; ++r) b[r] = a[r];
+    for (int j = 0; j < NB; ++j) {
+#pragma unroll
+      for (int r = 0; r < RV; ++r) c[j][r] = make_uint4(0, 0, 0, 0);
+      if (base + j >= n) continue;
+      en |= 1u << j;
+      const uint64_t d = list ? list[base + j] : pack_desc(kAtom, base + j, 0);
+      my_desc = lane == j ? d : my_desc;
+      const uint32_t op = desc_op(d);
+      if (op == kAtom) {
+        P::load_row(cv.atoms + size_t(desc_left(d)) * cv.vecs, c[j]);
+      } else {
+        uint4 a[RV], b[RV];
+        P::load_row(row_ptr(cv, desc_left(d)), a);
+        if (op == kAnd || op == kOr || op == kUntil) P::load_row(row_ptr(cv, desc_right(d)), b);
+        else {
+#pragma unroll
+          for (int r = 0; r < RV; ++r) b[r] = a[r];
+        }
+#pragma unroll
+        for (int r = 0; r < RV; ++r) c[j][r] = v_op<W>(op, a[r], b[r], lm[r], cv.steps);
       }
-#pragma unroll
-      for (int r = 0; r < RV; ++r) c[0][r] = v_op<W>(op, a[r], b[r], k.lm[r], cv.steps);
     }
-    const uint64_t dd[1] = {d};
-    P::template batch<1>(cv, k, c, dd, 1u);
+    P::batch(cv, k, c, my_desc, en, stage, pend, idr);
   }
+  P::flush(pend);
+  P::retire(cv, idr);
   if (implicit_atoms && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&cv.ctr->built, (unsigned long long)n);
-  (void)lane;
+}
+
+// ===========================================================================
+// Hole fixup: after a level, move the entries that lie above the level's dense
+// end into the holes below it (one warp per move): copy the CM row, its
+// provenance and slot index, and repoint the table slot to the new id.
+// ===========================================================================
+static __global__ void __launch_bounds__(256) k_fixup(CacheView cv, const uint2* moves, unsigned n) {
+  const int lane = threadIdx.x & 31;
+  const unsigned warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (unsigned m = warp; m < n; m += nwarps) {
+    const unsigned src = moves[m].x, dst = moves[m].y;
+    const uint4* a = cv.arena + size_t(src) * cv.vecs;
+    uint4* b = cv.arena + size_t(dst) * cv.vecs;
+    for (unsigned v = lane; v < cv.vecs; v += 32) b[v] = a[v];
+    if (lane == 0) {
+      cv.prov[dst] = cv.prov[src];
+      const unsigned sp = cv.slotpos[src];
+      cv.slotpos[dst] = sp;
+      const unsigned long long old = cv.table[sp];
+      if (uint32_t(old) == src + 1u) cv.table[sp] = (old & 0xFFFFFFFF00000000ull) | (unsigned long long)(dst + 1u);
+      else atomicExch(&cv.ctr->error, 3u);
+    }
+  }
 }
 
 // ===========================================================================
@@ -694,26 +895,33 @@ struct LaunchA {
 
 template <typename W, int RV>
 struct LaunchB {
+  static constexpr size_t kStageBytes = size_t(8) * PathB<W, RV>::kStage * sizeof(uint4);  // 8 warps
+  static void allow_smem(const void* fn) {
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+  }
   static cudaError_t desc_list(const CacheView& cv, const unsigned long long* list, const unsigned int* list_n,
                                unsigned int cap, unsigned int atoms, const LaunchCfg& lc) {
+    static bool once = (allow_smem((const void*)k_desc_b<W, RV>), true);
+    (void)once;
     const unsigned n = list ? cap : atoms;
-    const unsigned blocks = std::max(1u, std::min((n + 7u) / 8u, unsigned(lc.sms * 8)));
-    k_desc_b<W, RV><<<blocks, 256, 0, lc.stream>>>(cv, list, list_n, cap, atoms);
+    const unsigned per_block = 8u * PathB<W, RV>::NB;
+    const unsigned blocks = std::max(1u, std::min((n + per_block - 1) / per_block, unsigned(lc.sms * 3)));
+    k_desc_b<W, RV><<<blocks, 256, kStageBytes, lc.stream>>>(cv, list, list_n, cap, atoms);
     return cudaGetLastError();
   }
   static cudaError_t unary(const CacheView& cv, uint32_t first, uint32_t count, uint32_t ops, const LaunchCfg& lc) {
-    static int occ = occupancy_blocks((const void*)k_unary_b<W, RV>, 256, 0);
-    const unsigned blocks = std::max(1u, std::min((count + 7u) / 8u, unsigned(lc.sms * occ)));
-    k_unary_b<W, RV><<<blocks, 256, 0, lc.stream>>>(cv, first, count, ops);
+    static bool once = (allow_smem((const void*)k_unary_b<W, RV>), true);
+    (void)once;
+    static int occ = occupancy_blocks((const void*)k_unary_b<W, RV>, 256, kStageBytes);
+    const unsigned per_block = 8u * std::max(1, PathB<W, RV>::NB / 4);
+    const unsigned blocks = std::max(1u, std::min((count + per_block - 1) / per_block, unsigned(lc.sms * occ)));
+    k_unary_b<W, RV><<<blocks, 256, kStageBytes, lc.stream>>>(cv, first, count, ops);
     return cudaGetLastError();
   }
   static cudaError_t binary(const CacheView& cv, const BinaryPlan& plan, const LaunchCfg& lc) {
-    const size_t smem = size_t(plan.tile) * cv.vecs * sizeof(uint4);
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute((const void*)k_binary_b<W, RV>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-      attr = true;
-    }
+    static bool once = (allow_smem((const void*)k_binary_b<W, RV>), true);
+    (void)once;
+    const size_t smem = size_t(plan.tile) * cv.vecs * sizeof(uint4) + kStageBytes;
     const int occ = occupancy_blocks((const void*)k_binary_b<W, RV>, 256, smem);
     const unsigned long long blocks = std::max(1ull, std::min(plan.total_tiles, (unsigned long long)lc.sms * occ));
     k_binary_b<W, RV><<<unsigned(blocks), 256, smem, lc.stream>>>(cv, plan);
@@ -756,6 +964,14 @@ cudaError_t Kernels<W>::unary(const CacheView& cv, uint32_t first, uint32_t coun
 template <typename W>
 cudaError_t Kernels<W>::binary(const CacheView& cv, const BinaryPlan& plan, const LaunchCfg& lc) {
   LSYN_DISPATCH(cv.vecs, binary(cv, plan, lc), binary(cv, plan, lc))
+}
+
+template <typename W>
+cudaError_t Kernels<W>::fixup(const CacheView& cv, const uint2* moves, unsigned n, const LaunchCfg& lc) {
+  if (n == 0) return cudaSuccess;
+  const unsigned blocks = std::max(1u, std::min((n + 7u) / 8u, unsigned(lc.sms * 8)));
+  k_fixup<<<blocks, 256, 0, lc.stream>>>(cv, moves, n);
+  return cudaGetLastError();
 }
 
 template <typename W>

@@ -44,8 +44,9 @@ struct DevCounters {
   unsigned int error;            // probe ran over the whole table (cannot happen at load <= 0.9)
   unsigned int defer_n[2];       // deferred-list fills (ping-pong)
   unsigned int defer_overflow;   // a deferred list overflowed: exactness lost
-  unsigned int pad1;
+  unsigned int holes_n;          // id ranges reserved but left unused (hole log fill)
   unsigned long long built;      // candidates built in this level
+  unsigned long long inserted;   // new entries written in this level
   unsigned long long work[8];    // tile counters of the persistent launches
 };
 
@@ -67,6 +68,10 @@ struct CacheView {
   unsigned long long* defer_out; // deferred descriptors written by this launch
   unsigned int* defer_out_n;
   unsigned int defer_cap;
+  unsigned int* slotpos;         // [max_entries]: table slot of each entry (for hole fixup)
+  uint2* holes;                  // [hole_cap]: unused id ranges [x, y) left by warps
+  unsigned int hole_cap;
+  unsigned int chunk;            // ids a warp reserves per counter update (path B)
   int steps;                     // log-step count: 2^steps >= longest trace
   int early_exit;                // 1: stop at the first separating candidate
 };
@@ -113,6 +118,8 @@ struct Kernels {
   static cudaError_t unary(const CacheView& cv, uint32_t first, uint32_t count, uint32_t ops,
                            const LaunchCfg& lc);
   static cudaError_t binary(const CacheView& cv, const BinaryPlan& plan, const LaunchCfg& lc);
+  // Move entries src -> dst (pairs), repointing their table slots.
+  static cudaError_t fixup(const CacheView& cv, const uint2* moves, unsigned n, const LaunchCfg& lc);
   // Evaluate a postorder node list on every trace word: scratch [n_nodes][words].
   static cudaError_t eval(const uint4* atoms, const uint4* lenmask, unsigned vecs,
                           const int4* nodes, int n_nodes, int steps, W* scratch, W* out,
