@@ -237,6 +237,33 @@ lsyn_status lsyn_eval(const lsyn_problem* problem, const char* formula, void* ds
                       const lsyn_config* config);
 
 /*
+ * Formula evaluation that allocates no device memory (the paper has no
+ * counterpart; it is a service for callers that cannot call cudaMalloc, such
+ * as a process whose memory manager owns every device allocation, or a
+ * latency-critical loop where an allocation that may synchronise the device is
+ * not acceptable). Same result as lsyn_eval, on buffers the caller already
+ * holds on the current device:
+ *   atom_words  device, [n_props][n_traces] words of word_bits bits, row-major
+ *               by proposition (bit t of word (p, i): p holds at position t of
+ *               trace i); bits at positions >= the trace's length are ignored.
+ *   lengths     device, int32[n_traces]; each is clamped to 0..word_bits.
+ *   dst         device, n_traces words of word_bits bits: the formula's CM.
+ *   stream      cudaStream_t (NULL = legacy default stream); the call only
+ *               enqueues work, synchronise the stream before reading dst.
+ * Per-node scratch lives in a fixed 8 MiB device array inside the library,
+ * one per GPU, held until the process exits: (nodes x n_traces x word_bits/8)
+ * must not exceed 8 MiB and a formula may have at most 960 nodes, otherwise
+ * LSYN_E_INVAL with a message in lsyn_last_error(NULL). The first call on a
+ * device looks the array's device address up once (cudaGetSymbolAddress);
+ * make that first call before capturing the stream into a graph. Every call
+ * shares the array and it keeps the last call's contents (nothing in it needs
+ * clearing); calls that overlap on the GPU race on it. No cudaMalloc, cudaFree
+ * or other allocating routine is called.
+ */
+lsyn_status lsyn_eval_noalloc(int32_t n_props, int32_t n_traces, int32_t word_bits, const void* atom_words,
+                              const int32_t* lengths, const char* formula, void* dst, void* stream);
+
+/*
  * Host-only helper (no GPU needed): the number of candidates level k builds
  * when every level i < k holds level_sizes[i - 1] entries (k >= 2; and/or
  * counted once per unordered pair, U per ordered pair, unary once per entry).

@@ -67,6 +67,8 @@ struct Snap {
 
 }  // namespace
 
+std::string& lsyn::thread_error() { return g_create_error; }
+
 struct lsyn_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;

@@ -3,9 +3,13 @@
 #pragma once
 
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
 
 namespace lsyn {
+
+// This thread's message for lsyn_last_error(NULL).
+std::string& thread_error();
 
 // Operator codes stored in provenance records.
 enum : uint32_t {

@@ -101,6 +101,8 @@ def _load_library():
     lib.lsyn_entry_formula.argtypes = [vp, i32, i64, ctypes.c_char_p, ctypes.c_size_t]
     lib.lsyn_eval.restype = i32
     lib.lsyn_eval.argtypes = [P(lsyn_problem), ctypes.c_char_p, vp, P(lsyn_config)]
+    lib.lsyn_eval_noalloc.restype = i32
+    lib.lsyn_eval_noalloc.argtypes = [i32, i32, i32, vp, vp, ctypes.c_char_p, vp, vp]
     lib.lsyn_level_candidates.restype = i64
     lib.lsyn_level_candidates.argtypes = [P(i64), i32, ctypes.c_uint32]
     lib.lsyn_version.restype = ctypes.c_char_p
@@ -313,6 +315,16 @@ def lsyn_eval(problem: PackedProblem, formula: str, config: Optional[lsyn_config
                         ctypes.byref(config) if config is not None else None)
     _check(st, None)
     return out
+
+
+def lsyn_eval_noalloc(n_props: int, n_traces: int, word_bits: int, atom_words_dev: int, lengths_dev: int,
+                      formula: str, dst_dev: int, stream: int = 0) -> None:
+    """Evaluate a formula on traces already on the device, into a device buffer,
+    without allocating device memory (pointers are device addresses as ints).
+    Only enqueues work on ``stream``."""
+    st = _lib.lsyn_eval_noalloc(n_props, n_traces, word_bits, atom_words_dev, lengths_dev, formula.encode(),
+                                dst_dev, stream or None)
+    _check(st, None)
 
 
 def lsyn_level_candidates(level_sizes: Sequence[int], k: int, op_mask: int = OPS_ALL) -> int:
