@@ -52,6 +52,29 @@ struct Alloc {
   }
 };
 
+// Bit reversal within a word: the ABI numbers positions from the least
+// significant bit (bit t = position t); inside the library position 0 is the
+// most significant bit, as the paper writes characteristic sequences.
+uint32_t rev32(uint32_t x) {
+  x = ((x >> 1) & 0x55555555u) | ((x & 0x55555555u) << 1);
+  x = ((x >> 2) & 0x33333333u) | ((x & 0x33333333u) << 2);
+  x = ((x >> 4) & 0x0F0F0F0Fu) | ((x & 0x0F0F0F0Fu) << 4);
+  x = ((x >> 8) & 0x00FF00FFu) | ((x & 0x00FF00FFu) << 8);
+  return (x >> 16) | (x << 16);
+}
+
+uint64_t rev64(uint64_t x) { return (uint64_t(rev32(uint32_t(x))) << 32) | rev32(uint32_t(x >> 32)); }
+
+void reverse_words(void* data, size_t n_words, int word_bits) {
+  if (word_bits == 32) {
+    uint32_t* w = static_cast<uint32_t*>(data);
+    for (size_t i = 0; i < n_words; ++i) w[i] = rev32(w[i]);
+  } else {
+    uint64_t* w = static_cast<uint64_t*>(data);
+    for (size_t i = 0; i < n_words; ++i) w[i] = rev64(w[i]);
+  }
+}
+
 uint32_t mix32(uint32_t x) {
   x ^= x >> 16; x *= 0x7FEB352Du; x ^= x >> 15; x *= 0x846CA68Bu; x ^= x >> 16;
   return x;
@@ -357,20 +380,28 @@ void pack_host(const lsyn_problem* p, const Layout& L, unsigned vecs, std::vecto
   uint32_t* key = care + n32;
   uint32_t* mul = key + n32;
   const int per = p->word_bits / 32;  // 32-bit halves per word
+  // Words are stored position 0 first (most significant bit); the 32-bit
+  // halves of a 64-bit word are little-endian in memory.
+  auto store = [&](uint32_t* dst, int i, uint64_t w_lsb_first) {
+    if (per == 1) {
+      dst[i] = rev32(uint32_t(w_lsb_first));
+    } else {
+      const uint64_t r = rev64(w_lsb_first);
+      dst[2 * i] = uint32_t(r);
+      dst[2 * i + 1] = uint32_t(r >> 32);
+    }
+  };
   for (int i = 0; i < L.T; ++i) {
     const int len = p->lengths[i];
-    uint64_t m = len >= 64 ? ~0ull : ((1ull << len) - 1ull);
-    lm[i * per] = uint32_t(m);
-    if (per == 2) lm[i * per + 1] = uint32_t(m >> 32);
-    lab[i * per] = i < p->n_pos ? 1u : 0u;
-    care[i * per] = 1u;
+    const uint64_t m = len >= 64 ? ~0ull : ((1ull << len) - 1ull);  // positions 0..len-1
+    store(lm, i, m);
+    store(lab, i, i < p->n_pos ? 1ull : 0ull);  // the position-0 bit
+    store(care, i, 1ull);
     for (int q = 0; q < p->n_props; ++q) {
       uint64_t w;
       if (per == 1) w = static_cast<const uint32_t*>(p->atom_words)[size_t(q) * L.T + i];
       else w = static_cast<const uint64_t*>(p->atom_words)[size_t(q) * L.T + i];
-      w &= m;
-      (*atoms)[size_t(q) * n32 + i * per] = uint32_t(w);
-      if (per == 2) (*atoms)[size_t(q) * n32 + i * per + 1] = uint32_t(w >> 32);
+      store(atoms->data() + size_t(q) * n32, i, w & m);
     }
   }
   for (unsigned i = 0; i < n32; ++i) {
@@ -474,7 +505,7 @@ lsyn_status lsyn_create(const lsyn_problem* problem, const lsyn_config* config, 
   c->path = L.vecs_needed <= 8 ? 1 : 2;
   c->table_cap = best_cap;
   c->max_entries = unsigned(best_e);
-  c->defer_cap = 1u << 20;
+  c->defer_cap = unsigned(std::max(1ull << 16, std::min(1ull << 23, best_e / 16)));
   c->hole_cap = 1u << 16;
   c->move_cap = c->hole_cap * 32u;
 
@@ -835,7 +866,9 @@ lsyn_status lsyn_export_level(lsyn_ctx* c, int32_t k, int64_t first, int64_t cou
   cudaError_t e = cudaMemcpy2DAsync(dst, row, src, size_t(c->vecs) * 16, row, size_t(count),
                                     cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-  return e == cudaSuccess ? LSYN_OK : c->cuda_fail(e, "export");
+  if (e != cudaSuccess) return c->cuda_fail(e, "export");
+  reverse_words(dst, size_t(count) * size_t(c->T), c->word_bits);  // back to bit t = position t
+  return LSYN_OK;
 }
 
 lsyn_status lsyn_entry_formula(lsyn_ctx* c, int32_t k, int64_t index, char* buf, size_t cap) {
@@ -897,6 +930,7 @@ lsyn_status lsyn_eval(const lsyn_problem* problem, const char* formula, void* ds
     g_create_error = std::string("eval: ") + cudaGetErrorString(e);
     return LSYN_E_CUDA;
   }
+  reverse_words(host_out.data(), size_t(L.T), L.word_bits);  // back to bit t = position t
   memcpy(dst, host_out.data(), size_t(L.T) * (L.word_bits / 8));
   return LSYN_OK;
 }

@@ -28,49 +28,86 @@ template <> struct WordInfo<uint64_t> { static constexpr int kMaxSteps = 6; };
 
 // ---------------------------------------------------------------------------
 // Operators on one trace word ("Logical operations as bitwise operations").
-//   not  : complement, masked to the trace length (nothing holds past the end)
-//   X    : shift toward position 0 by one (the last position becomes false)
-//   F    : suffix-OR by doubling shifts: after the step with shift s every bit
-//          t holds the OR of positions [t, t + 2s)
-//   G    : not F not (suffix-AND), masked to the trace length
-//   U    : log-step doubling. R starts as psi and A as phi; the step with
-//          shift s sets R(t) |= A(t) & R(t + s) and then A(t) &= A(t + s), so
-//          afterwards R(t) says "psi at some j in [t, t + 2s) and phi on
-//          [t, j)" and A(t) says "phi on [t, t + 2s)".
-// `steps` is the smallest s with 2^s >= the longest trace.
+// Inside the library a characteristic sequence is stored most significant bit
+// first, as the paper writes it: position 0 is the top bit, position t is bit
+// (word_bits - 1 - t), so "position t + 1" is the next lower bit and positions
+// at or beyond the trace's end are the low padding bits, always 0.
+//
+// The enumeration kernels use these forms (w_op):
+//   not : ~a & lenmask
+//   X   : a << 1                        (position t takes position t + 1)
+//   F   : -(a & -a)                     (every bit from the lowest set bit up:
+//                                        "holds at t or at some later position")
+//   G   : not F not, masked to the trace length
+//   U   : B | (A & ((A|B) + B  ^  (A & ~B)))   with A = phi, B = psi.
+// F and U are suffix scans computed by the integer adder's carry chain: in
+// (A|B) + B a carry is generated where B holds and propagated where A holds, so
+// the carry into bit j says "psi at some later position with phi on every
+// position in between", and U_j = B_j | (A_j & carry_j).
+//
+// The formula evaluator (w_op_logstep) uses the paper's log-step forms instead:
+//   F: a |= a << s for s = 1, 2, 4, ...; U: R |= A & (R << s); A &= A << s
+// (R starts as psi, A as phi; R uses the old A). Both are checked against the
+// CPU oracle, so each formulation checks the other.
 // ---------------------------------------------------------------------------
 template <typename W>
-__device__ __forceinline__ W w_future(W a, int steps) {
+__device__ __forceinline__ W w_future(W a) {
+  return W(0) - (a & (W(0) - a));
+}
+
+template <typename W>
+__device__ __forceinline__ W w_until(W phi, W psi) {
+  const W cin = ((phi | psi) + psi) ^ (phi & ~psi);
+  return psi | (phi & cin);
+}
+
+template <typename W>
+__device__ __forceinline__ W w_op(uint32_t op, W a, W b, W lm, int /*steps*/) {
+  switch (op) {
+    case kNot: return ~a & lm;
+    case kAnd: return a & b;
+    case kOr: return a | b;
+    case kNext: return a << 1;
+    case kFuture: return w_future<W>(a);
+    case kGlobally: return ~w_future<W>(~a & lm) & lm;
+    case kUntil: return w_until<W>(a, b);
+    default: return W(0);
+  }
+}
+
+// `steps` is the smallest s with 2^s >= the longest trace.
+template <typename W>
+__device__ __forceinline__ W w_future_logstep(W a, int steps) {
 #pragma unroll
   for (int s = 0; s < WordInfo<W>::kMaxSteps; ++s)
-    if (s < steps) a |= a >> (1u << s);
+    if (s < steps) a |= a << (1u << s);
   return a;
 }
 
 template <typename W>
-__device__ __forceinline__ W w_until(W phi, W psi, int steps) {
+__device__ __forceinline__ W w_until_logstep(W phi, W psi, int steps) {
   W r = psi;
 #pragma unroll
   for (int s = 0; s < WordInfo<W>::kMaxSteps; ++s) {
     if (s < steps) {
       const unsigned sh = 1u << s;
-      r |= phi & (r >> sh);
-      phi &= phi >> sh;
+      r |= phi & (r << sh);
+      phi &= phi << sh;
     }
   }
   return r;
 }
 
 template <typename W>
-__device__ __forceinline__ W w_op(uint32_t op, W a, W b, W lm, int steps) {
+__device__ __forceinline__ W w_op_logstep(uint32_t op, W a, W b, W lm, int steps) {
   switch (op) {
     case kNot: return ~a & lm;
     case kAnd: return a & b;
     case kOr: return a | b;
-    case kNext: return a >> 1;
-    case kFuture: return w_future<W>(a, steps);
-    case kGlobally: return ~w_future<W>(~a & lm, steps) & lm;
-    case kUntil: return w_until<W>(a, b, steps);
+    case kNext: return a << 1;
+    case kFuture: return w_future_logstep<W>(a, steps);
+    case kGlobally: return ~w_future_logstep<W>(~a & lm, steps) & lm;
+    case kUntil: return w_until_logstep<W>(a, b, steps);
     default: return W(0);
   }
 }
@@ -133,8 +170,9 @@ __device__ __forceinline__ uint64_t h_fin(uint32_t hi, uint32_t lo) {
 }
 
 // Specification check (section "Synthesising linear temporal logic formulae
-// from examples", separation): bit 0 of every real trace word must equal its
-// label (1 for P, 0 for N). Returns nonzero on a mismatch in this vector.
+// from examples", separation): the position-0 bit of every real trace word must
+// equal its label (1 for P, 0 for N); `lab` and `care` hold that bit only.
+// Returns nonzero on a mismatch in this vector.
 __device__ __forceinline__ uint32_t spec_bad(uint4 c, uint4 lab, uint4 care) {
   return ((c.x ^ lab.x) & care.x) | ((c.y ^ lab.y) & care.y) | ((c.z ^ lab.z) & care.z) |
          ((c.w ^ lab.w) & care.w);
@@ -376,12 +414,13 @@ __device__ __forceinline__ uint32_t comp(const uint4& v, int i) {
   return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
 }
 
-// Bit 0 of every trace word of a vector, packed (word j -> bit j).
+// The position-0 bit (the top bit) of every trace word of a vector, packed
+// (word j -> bit j).
 template <typename W> __device__ __forceinline__ uint32_t bit0s(uint4 c);
 template <> __device__ __forceinline__ uint32_t bit0s<uint32_t>(uint4 c) {
-  return (c.x & 1u) | ((c.y & 1u) << 1) | ((c.z & 1u) << 2) | ((c.w & 1u) << 3);
+  return (c.x >> 31) | ((c.y >> 31) << 1) | ((c.z >> 31) << 2) | ((c.w >> 31) << 3);
 }
-template <> __device__ __forceinline__ uint32_t bit0s<uint64_t>(uint4 c) { return (c.x & 1u) | ((c.z & 1u) << 1); }
+template <> __device__ __forceinline__ uint32_t bit0s<uint64_t>(uint4 c) { return (c.y >> 31) | ((c.w >> 31) << 1); }
 
 template <typename W, int RV>
 struct PathB {
@@ -479,8 +518,9 @@ struct PathB {
       my_hi = lane == q ? hi : my_hi;
       bad |= ((bits ^ k.lab) != 0u ? 1u : 0u) << q;
     }
-    // Separation (section "Synthesising ... from examples"): bit 0 of every
-    // trace word equals the trace's label. Padding words are 0 with label 0.
+    // Separation (section "Synthesising ... from examples"): the position-0 bit
+    // of every trace word equals the trace's label. Padding words are 0 with
+    // label 0.
     bad = __reduce_or_sync(kFull, bad);
     const bool mine = lane < NB && ((en >> lane) & 1u);
     if (mine && !((bad >> lane) & 1u)) record_solution(cv, my_desc);
@@ -811,6 +851,389 @@ __global__ void __launch_bounds__(256, 3) k_desc_b(CacheView cv, const unsigned 
 }
 
 // ===========================================================================
+// Path C (CMs of exactly one 16-byte vector per lane: 32 vectors, 512 bytes for
+// 32-bit words): "hash first". A warp batch covers up to 32 candidates, one per
+// lane for probing. Candidates are not held while their probes are in flight:
+// the generator recomputes candidate q from operands kept in shared memory or
+// registers whenever it is needed (hashing, comparing, writing). Registers stay
+// few, so more warps fit, and each warp has up to 32 probes and 8 compare
+// reads in flight.
+// ===========================================================================
+template <typename W>
+struct PathC {
+  static constexpr int WPV = int(16 / sizeof(W));
+  static constexpr int kGroup = 8;             // compare reads staged together
+  static constexpr int kStage = kGroup * 32;   // uint4 of staging per warp
+
+  using Pending = typename PathB<W, 1>::Pending;
+  using Ids = typename PathB<W, 1>::Ids;
+
+  struct Consts {
+    uint4 mul;     // hash multipliers of this lane's 32-bit words
+    uint32_t lab;  // bit j: 1 iff word j of this lane's vector belongs to a positive trace
+  };
+
+  __device__ static void load_consts(const CacheView& cv, Consts& k) {
+    const int lane = threadIdx.x & 31;
+    k.mul = cv.hmul[lane];
+    k.lab = bit0s<W>(cv.label[lane]);
+  }
+
+  // The first (at most) kGroup set bits of m.
+  __device__ static uint32_t first_bits(uint32_t m) {
+    uint32_t g = 0;
+#pragma unroll
+    for (int i = 0; i < kGroup; ++i) {
+      const uint32_t b = m & (0u - m);
+      g |= b;
+      m ^= b;
+    }
+    return g;
+  }
+
+  // gen.compute(q): this lane's vector of candidate q (q warp-uniform);
+  // gen.desc(q): descriptor of candidate q. Candidates 0..n-1, bit q of `en`
+  // (warp-uniform) says candidate q is real.
+  template <class Gen>
+  __device__ static void batch(const CacheView& cv, const Consts& k, const Gen& gen, int n, uint32_t en,
+                               uint4* stage, Pending& pend, Ids& ids) {
+    const int lane = threadIdx.x & 31;
+    uint32_t my_lo = 0, my_hi = 0, bad = 0;
+    for (int q = 0; q < n; ++q) {
+      const uint4 c = gen.compute(q);
+      const uint64_t acc = h_mac(c, k.mul, 0ull);
+      const uint32_t lo = __reduce_add_sync(kFull, uint32_t(acc));
+      const uint32_t hi = __reduce_add_sync(kFull, uint32_t(acc >> 32));
+      my_lo = lane == q ? lo : my_lo;
+      my_hi = lane == q ? hi : my_hi;
+      bad |= ((bit0s<W>(c) ^ k.lab) != 0u ? 1u : 0u) << q;
+    }
+    // Separation (section "Synthesising ... from examples"): the position-0 bit
+    // of every trace word equals the trace's label. Padding words are 0 with
+    // label 0.
+    bad = __reduce_or_sync(kFull, bad);
+    const bool mine = lane < n && ((en >> lane) & 1u);
+    const uint64_t my_desc = gen.desc(lane < n ? lane : 0);
+    if (mine && !((bad >> lane) & 1u)) record_solution(cv, my_desc);
+
+    int state = mine ? PathB<W, 1>::kProbing : PathB<W, 1>::kDone;
+    constexpr int kProbing = PathB<W, 1>::kProbing, kDone = PathB<W, 1>::kDone,
+                  kClaimed = PathB<W, 1>::kClaimed, kDeferred = PathB<W, 1>::kDeferred;
+    const uint64_t h = h_fin(my_hi, my_lo);
+    const unsigned long long tag = (h >> 32) << 32;
+    unsigned long long pos = h & cv.table_mask;
+
+    // Twins inside the batch (equal hashes; common, since the batch's
+    // candidates share an operand): compare each with its lowest-lane twin in
+    // registers; an equal one is a duplicate and does not probe.
+    const uint32_t mine_mask = __ballot_sync(kFull, mine);
+    const uint32_t peers = __match_any_sync(kFull, (unsigned long long)h) & mine_mask;
+    const bool has_twin = mine && (peers & ((1u << lane) - 1u)) != 0u;
+    const int twin = __ffs(peers) - 1;
+    for (uint32_t m = __ballot_sync(kFull, has_twin); m; m &= m - 1u) {
+      const int q = __ffs(m) - 1;
+      const int p = __shfl_sync(kFull, twin, q);
+      const bool eq = !__any_sync(kFull, v_ne(gen.compute(q), gen.compute(p)) != 0u);
+      if (lane == q && eq) state = kDone;
+    }
+
+    // Publish the previous batch's slots before probing: this warp never
+    // meets its own pending inserts.
+    PathB<W, 1>::flush(pend);
+    uint32_t cmp_id = 0;
+    unsigned long long guard = 0;
+    while (true) {
+      bool need = false;
+      if (state == kProbing) {
+        // One atomic per probe: claims an empty slot, or returns what is there.
+        const unsigned long long sv = atomicCAS(cv.table + pos, 0ull, tag | kSlotPending);
+        if (sv == 0ull) {
+          state = kClaimed;
+        } else {
+          const uint32_t low = uint32_t(sv);
+          if ((sv & 0xFFFFFFFF00000000ull) != tag || low == kSlotTomb) pos = (pos + 1) & cv.table_mask;
+          else if (low == kSlotPending) state = kDeferred;
+          else {
+            need = true;
+            cmp_id = low - 1u;
+          }
+        }
+      }
+      uint32_t cm = __ballot_sync(kFull, need);
+      while (cm) {
+        const uint32_t grp = first_bits(cm);
+        cm ^= grp;
+        // Stage the stored rows (published before their slots; cp.async.cg
+        // reads them from L2), then recompute and compare.
+        int slot = 0;
+        for (uint32_t m = grp; m; m &= m - 1u, ++slot) {
+          const int q = __ffs(m) - 1;
+          const uint32_t id = __shfl_sync(kFull, cmp_id, q);
+          cp_async16(stage + slot * 32 + lane, row_ptr(cv, id) + lane);
+        }
+        cp_async_wait_all();
+        uint32_t ne = 0;
+        slot = 0;
+        for (uint32_t m = grp; m; m &= m - 1u, ++slot) {
+          const int q = __ffs(m) - 1;
+          ne |= (v_ne(stage[slot * 32 + lane], gen.compute(q)) != 0u ? 1u : 0u) << q;
+        }
+        ne = __reduce_or_sync(kFull, ne);
+        if ((grp >> lane) & 1u) {
+          if (!((ne >> lane) & 1u)) state = kDone;  // equal CM already cached
+          else pos = (pos + 1) & cv.table_mask;
+        }
+      }
+      if (!__any_sync(kFull, state == kProbing)) break;
+      if (++guard > cv.table_mask) {  // every slot seen: cannot happen at load <= 0.9
+        if (lane == 0) atomicExch(&cv.ctr->error, 1u);
+        if (state == kProbing) state = kDone;
+      }
+    }
+
+    const uint32_t claim = __ballot_sync(kFull, state == kClaimed);
+    const unsigned n_claim = unsigned(__popc(claim));
+    const unsigned have = ids.end - ids.next;  // warp-uniform
+    unsigned base = 0;
+    if (n_claim > have && lane == 0) base = atomicAdd(&cv.ctr->n_entries, max(cv.chunk, n_claim - have));
+    if (claim) {
+      unsigned fresh = 0;
+      if (n_claim > have) fresh = __shfl_sync(kFull, base, 0);
+      unsigned rank = 0;
+      for (uint32_t m = claim; m; m &= m - 1u, ++rank) {
+        const int q = __ffs(m) - 1;
+        const unsigned id = rank < have ? ids.next + rank : fresh + (rank - have);
+        if (id < cv.max_entries) cv.arena[size_t(id) * cv.vecs + lane] = gen.compute(q);
+      }
+      const unsigned my_rank = unsigned(__popc(claim & ((1u << lane) - 1u)));
+      const unsigned my_id = my_rank < have ? ids.next + my_rank : fresh + (my_rank - have);
+      if (n_claim > have) {
+        ids.next = fresh + (n_claim - have);
+        ids.end = fresh + max(cv.chunk, n_claim - have);
+      } else {
+        ids.next += n_claim;
+      }
+      ids.inserted += n_claim;
+      if (state == kClaimed) {
+        unsigned long long* slot = cv.table + pos;
+        if (my_id < cv.max_entries) {
+          cv.prov[my_id] = my_desc;
+          cv.slotpos[my_id] = unsigned(pos);
+          pend.slot = slot;
+          pend.val = tag | (unsigned long long)(my_id + 1u);
+        } else {
+          st_relaxed(slot, tag | kSlotTomb);  // nothing to order: no CM behind it
+          atomicExch(&cv.ctr->full, 1u);
+        }
+      }
+    }
+    if (state == kDeferred) defer(cv, my_desc);
+  }
+};
+
+// Candidate generators of path C.
+template <typename W>
+struct BinaryGen {
+  const uint4* a_rows;  // shared memory: row p of the group at a_rows[p * 32]
+  uint4 b;              // this lane's vector of the streamed operand
+  uint32_t a0, b_id;    // cache id of row 0 of the group, and of b
+  int steps, lane;
+  __device__ uint4 compute(int q) const {
+    const uint4 a = a_rows[(q >> 2) * 32 + lane];
+    switch (q & 3) {
+      case 0: return v_op<W>(kAnd, a, b, b, steps);
+      case 1: return v_op<W>(kOr, a, b, b, steps);
+      case 2: return v_op<W>(kUntil, a, b, b, steps);
+      default: return v_op<W>(kUntil, b, a, b, steps);
+    }
+  }
+  __device__ uint64_t desc(int q) const {
+    const uint32_t ai = a0 + uint32_t(q >> 2);
+    switch (q & 3) {
+      case 0: return pack_desc(kAnd, ai, b_id);
+      case 1: return pack_desc(kOr, ai, b_id);
+      case 2: return pack_desc(kUntil, ai, b_id);
+      default: return pack_desc(kUntil, b_id, ai);
+    }
+  }
+};
+
+template <typename W>
+struct UnaryGen {
+  const uint4* rows;  // shared memory: row p at rows[p * 32]
+  uint4 lm;
+  uint32_t id0;       // cache id of row 0
+  int steps, lane;
+  __device__ uint4 compute(int q) const {
+    return v_op<W>(unary_code(q & 3), rows[(q >> 2) * 32 + lane], make_uint4(0, 0, 0, 0), lm, steps);
+  }
+  __device__ uint64_t desc(int q) const { return pack_desc(unary_code(q & 3), id0 + uint32_t(q >> 2), 0); }
+};
+
+template <typename W>
+struct ListGen {
+  const CacheView* cv;
+  const uint64_t* d;  // shared memory: the group's descriptors
+  uint4 lm;
+  int lane;
+  __device__ uint4 compute(int q) const {
+    const uint64_t dd = d[q];
+    const uint32_t op = desc_op(dd);
+    if (op == kAtom) return __ldg(cv->atoms + size_t(desc_left(dd)) * cv->vecs + lane);
+    const uint4 a = __ldg(row_ptr(*cv, desc_left(dd)) + lane);
+    const uint4 b = (op == kAnd || op == kOr || op == kUntil) ? __ldg(row_ptr(*cv, desc_right(dd)) + lane) : a;
+    return v_op<W>(op, a, b, lm, cv->steps);
+  }
+  __device__ uint64_t desc(int q) const { return d[q]; }
+};
+
+template <typename W>
+__global__ void __launch_bounds__(256, 4) k_unary_c(CacheView cv, uint32_t first, uint32_t count, uint32_t ops) {
+  using P = PathC<W>;
+  constexpr int ROWS = 4;  // 16 candidates per batch
+  extern __shared__ uint4 smem[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  uint4* rows = smem + wib * (ROWS * 32 + P::kStage);
+  uint4* stage = rows + ROWS * 32;
+  typename P::Consts k;
+  P::load_consts(cv, k);
+  UnaryGen<W> gen;
+  gen.rows = rows;
+  gen.lm = cv.lenmask[lane];
+  gen.steps = cv.steps;
+  gen.lane = lane;
+  uint32_t en_ops = 0;  // candidate q is real iff its operator is enabled
+#pragma unroll
+  for (int q = 0; q < 4 * ROWS; ++q) en_ops |= ((ops >> (q & 3)) & 1u) << q;
+  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  unsigned long long built = 0;
+  typename P::Pending pend;
+  typename P::Ids idr;
+  uint32_t iter = 0;
+  for (uint32_t base = warp * ROWS; base < count; base += nwarps * ROWS, ++iter) {
+    if ((iter & 3u) == 0 && __any_sync(kFull, stop_requested(cv))) break;
+    const uint32_t nrows = min(uint32_t(ROWS), count - base);
+#pragma unroll
+    for (int p = 0; p < ROWS; ++p)
+      if (p < int(nrows)) rows[p * 32 + lane] = __ldg(row_ptr(cv, first + base + p) + lane);
+    __syncwarp();
+    gen.id0 = first + base;
+    const uint32_t en = en_ops & ((nrows >= 8u ? 0xFFFFFFFFu : ((1u << (4 * nrows)) - 1u)));
+    P::batch(cv, k, gen, int(4 * nrows), en, stage, pend, idr);
+    built += __popc(en);
+    __syncwarp();
+  }
+  PathB<W, 1>::flush(pend);
+  PathB<W, 1>::retire(cv, idr);
+  if (lane == 0 && built) atomicAdd(&cv.ctr->built, built);
+}
+
+template <typename W>
+__global__ void __launch_bounds__(256, 4) k_binary_c(CacheView cv, BinaryPlan plan) {
+  using P = PathC<W>;
+  constexpr int PAIRS = 8;  // 32 candidates per batch
+  extern __shared__ uint4 smem[];
+  __shared__ unsigned long long s_tile;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  uint4* s_left = smem;  // plan.tile rows x 32 vectors
+  uint4* stage = smem + size_t(plan.tile) * 32 + warp * P::kStage;
+  typename P::Consts k;
+  P::load_consts(cv, k);
+  uint32_t en_ops = 0;
+#pragma unroll
+  for (int q = 0; q < 4 * PAIRS; ++q) en_ops |= ((plan.ops >> (q & 3)) & 1u) << q;
+  BinaryGen<W> gen;
+  gen.steps = cv.steps;
+  gen.lane = lane;
+  unsigned long long built = 0;
+  typename P::Pending pend;
+  typename P::Ids idr;
+  while (true) {
+    if (threadIdx.x == 0) {
+      unsigned long long t = atomicAdd(&cv.ctr->work[plan.work_slot], 1ull);
+      if (stop_requested(cv)) t = plan.total_tiles;
+      s_tile = t;
+    }
+    __syncthreads();
+    const unsigned long long tile = s_tile;
+    if (tile >= plan.total_tiles) break;
+    int sp = 0;
+    while (sp + 1 < plan.n_splits && plan.s[sp + 1].tiles_begin <= tile) ++sp;
+    const Split& S = plan.s[sp];
+    const unsigned long long t = tile - S.tiles_begin;
+    const uint32_t lt = uint32_t(t / S.rt_tiles);
+    const uint32_t rt = uint32_t(t - (unsigned long long)lt * S.rt_tiles);
+    const bool skip = S.tri && rt < lt;
+    const uint32_t l0 = lt * plan.tile, r0 = rt * plan.tile;
+    const uint32_t ln = skip ? 0u : min(plan.tile, S.left_n - l0);
+    const uint32_t rn = skip ? 0u : min(plan.tile, S.right_n - r0);
+    {
+      const uint4* src = row_ptr(cv, S.left_start + l0);
+      const uint32_t total = ln * 32u;
+      for (uint32_t i = threadIdx.x; i < total; i += blockDim.x) s_left[i] = __ldg(src + i);
+    }
+    __syncthreads();
+    for (uint32_t rr = warp; rr < rn; rr += nwarps) {
+      if (__any_sync(kFull, stop_requested(cv))) break;
+      gen.b_id = S.right_start + r0 + rr;
+      gen.b = __ldg(row_ptr(cv, gen.b_id) + lane);
+      for (uint32_t li = 0; li < ln; li += PAIRS) {
+        // pairs li .. li + np - 1 of the staged rows; same level: only a < b
+        uint32_t np = min(uint32_t(PAIRS), ln - li);
+        gen.a0 = S.left_start + l0 + li;
+        if (S.tri) np = gen.b_id > gen.a0 ? min(np, gen.b_id - gen.a0) : 0u;
+        if (np == 0) break;  // rows ascend: no later row pairs with b either
+        gen.a_rows = s_left + li * 32;
+        const uint32_t en = en_ops & (np >= 8u ? 0xFFFFFFFFu : ((1u << (4 * np)) - 1u));
+        P::batch(cv, k, gen, int(4 * np), en, stage, pend, idr);
+        built += __popc(en);
+      }
+    }
+    __syncthreads();
+  }
+  PathB<W, 1>::flush(pend);
+  PathB<W, 1>::retire(cv, idr);
+  if (lane == 0 && built) atomicAdd(&cv.ctr->built, built);
+}
+
+template <typename W>
+__global__ void __launch_bounds__(256, 4) k_desc_c(CacheView cv, const unsigned long long* list,
+                                                   const unsigned int* list_n, unsigned int list_cap,
+                                                   unsigned int implicit_atoms) {
+  using P = PathC<W>;
+  constexpr int N = 32;
+  extern __shared__ uint4 smem[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  uint4* stage = smem + wib * (P::kStage + N / 2);
+  uint64_t* dbuf = reinterpret_cast<uint64_t*>(stage + P::kStage);  // N descriptors
+  typename P::Consts k;
+  P::load_consts(cv, k);
+  ListGen<W> gen;
+  gen.cv = &cv;
+  gen.d = dbuf;
+  gen.lm = cv.lenmask[lane];
+  gen.lane = lane;
+  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  unsigned n = implicit_atoms;
+  if (list) n = min(*list_n, list_cap);
+  typename P::Pending pend;
+  typename P::Ids idr;
+  for (uint32_t base = warp * N; base < n; base += nwarps * N) {
+    if (__any_sync(kFull, stop_requested(cv))) break;
+    const uint32_t cnt = min(uint32_t(N), n - base);
+    if (lane < int(cnt)) dbuf[lane] = list ? list[base + lane] : pack_desc(kAtom, base + lane, 0);
+    __syncwarp();
+    P::batch(cv, k, gen, int(cnt), cnt >= 32u ? 0xFFFFFFFFu : ((1u << cnt) - 1u), stage, pend, idr);
+    __syncwarp();
+  }
+  PathB<W, 1>::flush(pend);
+  PathB<W, 1>::retire(cv, idr);
+  if (implicit_atoms && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&cv.ctr->built, (unsigned long long)n);
+}
+
+// ===========================================================================
 // Hole fixup: after a level, move the entries that lie above the level's dense
 // end into the holes below it (one warp per move): copy the CM row, its
 // provenance and slot index, and repoint the table slot to the new id.
@@ -836,9 +1259,9 @@ static __global__ void __launch_bounds__(256) k_fixup(CacheView cv, const uint2*
 }
 
 // ===========================================================================
-// Formula evaluation: one thread per trace word walks a postorder node list
-// (x = op, y = left node, z = right node, w = proposition); scratch holds one
-// row of words per node.
+// Formula evaluation with the paper's log-step operators: one thread per trace
+// word walks a postorder node list (x = op, y = left node, z = right node,
+// w = proposition); scratch holds one row of words per node.
 // ===========================================================================
 template <typename W>
 __global__ void k_eval(const W* atoms, const W* lenmask, unsigned words, const int4* nodes, int n_nodes, int steps,
@@ -853,7 +1276,7 @@ __global__ void k_eval(const W* atoms, const W* lenmask, unsigned words, const i
     else {
       const W a = scratch[size_t(nd.y) * words + t];
       const W b = nd.z >= 0 ? scratch[size_t(nd.z) * words + t] : a;
-      v = w_op<W>(uint32_t(nd.x), a, b, lm, steps);
+      v = w_op_logstep<W>(uint32_t(nd.x), a, b, lm, steps);
     }
     scratch[size_t(i) * words + t] = v;
   }
@@ -930,6 +1353,36 @@ struct LaunchB {
 };
 
 template <typename W>
+struct LaunchC {
+  static constexpr size_t kUnarySmem = size_t(8) * (4 * 32 + PathC<W>::kStage) * sizeof(uint4);
+  static constexpr size_t kDescSmem = size_t(8) * (PathC<W>::kStage + 16) * sizeof(uint4);
+  static constexpr size_t kStageSmem = size_t(8) * PathC<W>::kStage * sizeof(uint4);
+  static cudaError_t desc_list(const CacheView& cv, const unsigned long long* list, const unsigned int* list_n,
+                               unsigned int cap, unsigned int atoms, const LaunchCfg& lc) {
+    const unsigned n = list ? cap : atoms;
+    const unsigned blocks = std::max(1u, std::min((n + 255u) / 256u, unsigned(lc.sms * 4)));
+    k_desc_c<W><<<blocks, 256, kDescSmem, lc.stream>>>(cv, list, list_n, cap, atoms);
+    return cudaGetLastError();
+  }
+  static cudaError_t unary(const CacheView& cv, uint32_t first, uint32_t count, uint32_t ops, const LaunchCfg& lc) {
+    static int occ = occupancy_blocks((const void*)k_unary_c<W>, 256, kUnarySmem);
+    const unsigned blocks = std::max(1u, std::min((count + 31u) / 32u, unsigned(lc.sms * occ)));
+    k_unary_c<W><<<blocks, 256, kUnarySmem, lc.stream>>>(cv, first, count, ops);
+    return cudaGetLastError();
+  }
+  static cudaError_t binary(const CacheView& cv, const BinaryPlan& plan, const LaunchCfg& lc) {
+    static bool once = (cudaFuncSetAttribute((const void*)k_binary_c<W>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024), true);
+    (void)once;
+    const size_t smem = size_t(plan.tile) * 32 * sizeof(uint4) + kStageSmem;
+    const int occ = occupancy_blocks((const void*)k_binary_c<W>, 256, smem);
+    const unsigned long long blocks = std::max(1ull, std::min(plan.total_tiles, (unsigned long long)lc.sms * occ));
+    k_binary_c<W><<<unsigned(blocks), 256, smem, lc.stream>>>(cv, plan);
+    return cudaGetLastError();
+  }
+};
+
+template <typename W>
 int Kernels<W>::path_for(unsigned vecs) {
   if (vecs == 1 || vecs == 2 || vecs == 4 || vecs == 8) return 1;
   if (vecs == 32 || vecs == 64 || vecs == 128 || vecs == 256) return 2;
@@ -942,7 +1395,7 @@ int Kernels<W>::path_for(unsigned vecs) {
     case 2: return LaunchA<W, 2>::CALL_A;               \
     case 4: return LaunchA<W, 4>::CALL_A;               \
     case 8: return LaunchA<W, 8>::CALL_A;               \
-    case 32: return LaunchB<W, 1>::CALL_B;              \
+    case 32: return LaunchC<W>::CALL_B;                 \
     case 64: return LaunchB<W, 2>::CALL_B;              \
     case 128: return LaunchB<W, 4>::CALL_B;             \
     case 256: return LaunchB<W, 8>::CALL_B;             \

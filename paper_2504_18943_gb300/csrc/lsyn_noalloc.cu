@@ -53,6 +53,9 @@ cudaError_t scratch_address(int device, void** out) {
   return cudaSuccess;
 }
 
+__device__ __forceinline__ uint32_t reverse_bits(uint32_t x) { return __brev(x); }
+__device__ __forceinline__ uint64_t reverse_bits(uint64_t x) { return __brevll(x); }
+
 template <typename W>
 __global__ void k_eval_noalloc(const W* atoms, const int32_t* lengths, unsigned n_traces, NodeTable nodes,
                                int n_nodes, W* scratch, W* out) {
@@ -60,22 +63,23 @@ __global__ void k_eval_noalloc(const W* atoms, const int32_t* lengths, unsigned 
   if (t >= n_traces) return;
   constexpr int kBits = int(sizeof(W) * 8);
   const int len = lengths[t];
-  const W lm = len >= kBits ? ~W(0) : len <= 0 ? W(0) : ((W(1) << len) - W(1));
+  // Length mask in the library's order (position 0 = top bit).
+  const W lm = len >= kBits ? ~W(0) : len <= 0 ? W(0) : ~(~W(0) >> len);
   for (int i = 0; i < n_nodes; ++i) {
     const uint32_t nd = nodes.n[i];
     const uint32_t op = nd & 7u;
     W v;
     if (op == lsyn::kAtom) {
-      v = atoms[size_t(nd >> 24) * n_traces + t] & lm;
+      v = reverse_bits(atoms[size_t(nd >> 24) * n_traces + t]) & lm;  // input: bit t = position t
     } else {
       const W a = scratch[size_t((nd >> 3) & 1023u) * n_traces + t];
       const uint32_t rb = (nd >> 13) & 2047u;
       const W b = rb ? scratch[size_t(rb - 1u) * n_traces + t] : a;
-      v = lsyn::w_op<W>(op, a, b, lm, lsyn::WordInfo<W>::kMaxSteps);
+      v = lsyn::w_op_logstep<W>(op, a, b, lm, lsyn::WordInfo<W>::kMaxSteps);
     }
     scratch[size_t(i) * n_traces + t] = v;
   }
-  out[t] = scratch[size_t(n_nodes - 1) * n_traces + t];
+  out[t] = reverse_bits(scratch[size_t(n_nodes - 1) * n_traces + t]);  // output: bit t = position t
 }
 
 bool parse_nodes(const char* s, int n_props, std::vector<uint32_t>* out, std::string* err);
