@@ -143,7 +143,8 @@ typedef struct {
   double ms;              /* wall time of the level (host clock, includes the final sync) */
   double kernel_ms[4];    /* with timing=1: device time of the unary, binary, resolve and other launches */
   double bytes_alg;       /* algorithmic bytes of the level (operand reads, probes, compares, inserts) */
-  double bytes_binary;    /* the part of bytes_alg moved by the binary-operator launches */
+  double bytes_binary;    /* the part of bytes_alg moved by the binary-operator launch */
+  double bytes_unary;     /* the part of bytes_alg moved by the unary-operator launch */
   int32_t launches;       /* kernel launches issued for this level */
   int32_t reserved;
 } lsyn_level_stats;

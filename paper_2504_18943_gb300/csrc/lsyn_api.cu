@@ -616,7 +616,7 @@ lsyn_status lsyn_enumerate_level(lsyn_ctx* c, int32_t k, lsyn_level_stats* out) 
   if ((e = take_snap()) != cudaSuccess) return c->cuda_fail(e, "snapshot");  // snap 0: before work
 
   CacheView cv = c->view(c->defer[0], &c->ctr->defer_n[0]);
-  int binary_snap = -1;
+  int binary_snap = -1, unary_snap = -1;
   double op_bytes_unary = 0, op_bytes_binary = 0;
   const double M = double(c->vecs) * 16.0;
   if (k == 1) {
@@ -640,6 +640,7 @@ lsyn_status lsyn_enumerate_level(lsyn_ctx* c, int32_t k, lsyn_level_stats* out) 
       if (e != cudaSuccess) return c->cuda_fail(e, "unary kernel");
       ev_end(0);
       if ((e = take_snap()) != cudaSuccess) return c->cuda_fail(e, "snapshot");
+      unary_snap = snap - 1;
       op_bytes_unary = double(prev_n) * M;
     }
     const uint32_t bops = ((m & LSYN_OP_AND) ? 1u : 0u) | ((m & LSYN_OP_OR) ? 2u : 0u) | ((m & LSYN_OP_U) ? 12u : 0u);
@@ -793,13 +794,18 @@ lsyn_status lsyn_enumerate_level(lsyn_ctx* c, int32_t k, lsyn_level_stats* out) 
     out->launches = launches;
     const double C = double(h.built), U = double(unique);
     out->bytes_alg = op_bytes_unary + op_bytes_binary + C * 32.0 + (C - U) * M + U * (M + 16.0);
-    if (binary_snap >= 0) {
-      const DevCounters& b0 = c->h_snap[binary_snap - 1].c;
-      const DevCounters& b1 = c->h_snap[binary_snap].c;
-      const double Cb = double(b1.built - b0.built);
-      const double Ub = double(b1.inserted - b0.inserted);
-      out->bytes_binary = op_bytes_binary + Cb * 32.0 + (Cb - Ub) * M + Ub * (M + 16.0);
-    }
+    // Per launch, from its exact built / inserted counters: operands, one table
+    // sector per candidate, a compare read per duplicate, CM + provenance +
+    // slot per insert.
+    auto launch_bytes = [&](int sn, double operands) {
+      const DevCounters& b0 = c->h_snap[sn - 1].c;
+      const DevCounters& b1 = c->h_snap[sn].c;
+      const double Cl = double(b1.built - b0.built);
+      const double Ul = double(b1.inserted - b0.inserted);
+      return operands + Cl * 32.0 + (Cl - Ul) * M + Ul * (M + 16.0);
+    };
+    if (binary_snap >= 0) out->bytes_binary = launch_bytes(binary_snap, op_bytes_binary);
+    if (unary_snap >= 0) out->bytes_unary = launch_bytes(unary_snap, op_bytes_unary);
     if (c->timing) {
       for (int i = 0; i < evn; ++i) {
         float ms = 0;

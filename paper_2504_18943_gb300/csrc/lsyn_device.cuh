@@ -894,19 +894,28 @@ struct PathC {
   // gen.compute(q): this lane's vector of candidate q (q warp-uniform);
   // gen.desc(q): descriptor of candidate q. Candidates 0..n-1, bit q of `en`
   // (warp-uniform) says candidate q is real.
-  template <class Gen>
+  // kEarlyPublish: publish the previous batch's slots before probing (for
+  // generators whose consecutive batches share an operand, so that a warp never
+  // defers on its own inserts); otherwise after probing, when the fence no
+  // longer waits for those stores.
+  template <bool kEarlyPublish, class Gen>
   __device__ static void batch(const CacheView& cv, const Consts& k, const Gen& gen, int n, uint32_t en,
                                uint4* stage, Pending& pend, Ids& ids) {
     const int lane = threadIdx.x & 31;
     uint32_t my_lo = 0, my_hi = 0, bad = 0;
-    for (int q = 0; q < n; ++q) {
-      const uint4 c = gen.compute(q);
-      const uint64_t acc = h_mac(c, k.mul, 0ull);
-      const uint32_t lo = __reduce_add_sync(kFull, uint32_t(acc));
-      const uint32_t hi = __reduce_add_sync(kFull, uint32_t(acc >> 32));
-      my_lo = lane == q ? lo : my_lo;
-      my_hi = lane == q ? hi : my_hi;
-      bad |= ((bit0s<W>(c) ^ k.lab) != 0u ? 1u : 0u) << q;
+    for (int q0 = 0; q0 < n; q0 += 4) {  // n is a multiple of 4: four operators per operand group
+      uint4 c4[4];
+      gen.compute4(q0, c4);
+#pragma unroll
+      for (int o = 0; o < 4; ++o) {
+        const int q = q0 + o;
+        const uint64_t acc = h_mac(c4[o], k.mul, 0ull);
+        const uint32_t lo = __reduce_add_sync(kFull, uint32_t(acc));
+        const uint32_t hi = __reduce_add_sync(kFull, uint32_t(acc >> 32));
+        my_lo = lane == q ? lo : my_lo;
+        my_hi = lane == q ? hi : my_hi;
+        bad |= ((bit0s<W>(c4[o]) ^ k.lab) != 0u ? 1u : 0u) << q;
+      }
     }
     // Separation (section "Synthesising ... from examples"): the position-0 bit
     // of every trace word equals the trace's label. Padding words are 0 with
@@ -937,9 +946,7 @@ struct PathC {
       if (lane == q && eq) state = kDone;
     }
 
-    // Publish the previous batch's slots before probing: this warp never
-    // meets its own pending inserts.
-    PathB<W, 1>::flush(pend);
+    if (kEarlyPublish) PathB<W, 1>::flush(pend);
     uint32_t cmp_id = 0;
     unsigned long long guard = 0;
     while (true) {
@@ -996,6 +1003,7 @@ struct PathC {
     const unsigned have = ids.end - ids.next;  // warp-uniform
     unsigned base = 0;
     if (n_claim > have && lane == 0) base = atomicAdd(&cv.ctr->n_entries, max(cv.chunk, n_claim - have));
+    if (!kEarlyPublish) PathB<W, 1>::flush(pend);  // overlaps the id reservation above
     if (claim) {
       unsigned fresh = 0;
       if (n_claim > have) fresh = __shfl_sync(kFull, base, 0);
@@ -1038,6 +1046,13 @@ struct BinaryGen {
   uint4 b;              // this lane's vector of the streamed operand
   uint32_t a0, b_id;    // cache id of row 0 of the group, and of b
   int steps, lane;
+  __device__ void compute4(int q0, uint4 (&c)[4]) const {
+    const uint4 a = a_rows[(q0 >> 2) * 32 + lane];
+    c[0] = v_op<W>(kAnd, a, b, b, steps);
+    c[1] = v_op<W>(kOr, a, b, b, steps);
+    c[2] = v_op<W>(kUntil, a, b, b, steps);
+    c[3] = v_op<W>(kUntil, b, a, b, steps);
+  }
   __device__ uint4 compute(int q) const {
     const uint4 a = a_rows[(q >> 2) * 32 + lane];
     switch (q & 3) {
@@ -1064,6 +1079,13 @@ struct UnaryGen {
   uint4 lm;
   uint32_t id0;       // cache id of row 0
   int steps, lane;
+  __device__ void compute4(int q0, uint4 (&c)[4]) const {
+    const uint4 a = rows[(q0 >> 2) * 32 + lane];
+    c[0] = v_op<W>(kNot, a, a, lm, steps);
+    c[1] = v_op<W>(kNext, a, a, lm, steps);
+    c[2] = v_op<W>(kFuture, a, a, lm, steps);
+    c[3] = v_op<W>(kGlobally, a, a, lm, steps);
+  }
   __device__ uint4 compute(int q) const {
     return v_op<W>(unary_code(q & 3), rows[(q >> 2) * 32 + lane], make_uint4(0, 0, 0, 0), lm, steps);
   }
@@ -1076,6 +1098,10 @@ struct ListGen {
   const uint64_t* d;  // shared memory: the group's descriptors
   uint4 lm;
   int lane;
+  __device__ void compute4(int q0, uint4 (&c)[4]) const {
+#pragma unroll
+    for (int o = 0; o < 4; ++o) c[o] = compute(q0 + o);
+  }
   __device__ uint4 compute(int q) const {
     const uint64_t dd = d[q];
     const uint32_t op = desc_op(dd);
@@ -1120,7 +1146,7 @@ __global__ void __launch_bounds__(256, 4) k_unary_c(CacheView cv, uint32_t first
     __syncwarp();
     gen.id0 = first + base;
     const uint32_t en = en_ops & ((nrows >= 8u ? 0xFFFFFFFFu : ((1u << (4 * nrows)) - 1u)));
-    P::batch(cv, k, gen, int(4 * nrows), en, stage, pend, idr);
+    P::template batch<false>(cv, k, gen, int(4 * nrows), en, stage, pend, idr);
     built += __popc(en);
     __syncwarp();
   }
@@ -1135,7 +1161,7 @@ __global__ void __launch_bounds__(256, 4) k_binary_c(CacheView cv, BinaryPlan pl
   constexpr int PAIRS = 8;  // 32 candidates per batch
   extern __shared__ uint4 smem[];
   __shared__ unsigned long long s_tile;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint4* s_left = smem;  // plan.tile rows x 32 vectors
   uint4* stage = smem + size_t(plan.tile) * 32 + warp * P::kStage;
   typename P::Consts k;
@@ -1143,6 +1169,7 @@ __global__ void __launch_bounds__(256, 4) k_binary_c(CacheView cv, BinaryPlan pl
   uint32_t en_ops = 0;
 #pragma unroll
   for (int q = 0; q < 4 * PAIRS; ++q) en_ops |= ((plan.ops >> (q & 3)) & 1u) << q;
+  __shared__ unsigned s_row;
   BinaryGen<W> gen;
   gen.steps = cv.steps;
   gen.lane = lane;
@@ -1152,8 +1179,9 @@ __global__ void __launch_bounds__(256, 4) k_binary_c(CacheView cv, BinaryPlan pl
   while (true) {
     if (threadIdx.x == 0) {
       unsigned long long t = atomicAdd(&cv.ctr->work[plan.work_slot], 1ull);
-      if (stop_requested(cv)) t = plan.total_tiles;
+      if (stop_requested(cv)) t = plan.total_tiles;  // early exit is polled once per tile
       s_tile = t;
+      s_row = 0;
     }
     __syncthreads();
     const unsigned long long tile = s_tile;
@@ -1174,8 +1202,13 @@ __global__ void __launch_bounds__(256, 4) k_binary_c(CacheView cv, BinaryPlan pl
       for (uint32_t i = threadIdx.x; i < total; i += blockDim.x) s_left[i] = __ldg(src + i);
     }
     __syncthreads();
-    for (uint32_t rr = warp; rr < rn; rr += nwarps) {
-      if (__any_sync(kFull, stop_requested(cv))) break;
+    while (true) {
+      // streamed rows are handed out one at a time: warps that meet more
+      // duplicates (or more inserts) do not hold the others at the barrier
+      unsigned rr = 0;
+      if (lane == 0) rr = atomicAdd(&s_row, 1u);
+      rr = __shfl_sync(kFull, rr, 0);
+      if (rr >= rn) break;
       gen.b_id = S.right_start + r0 + rr;
       gen.b = __ldg(row_ptr(cv, gen.b_id) + lane);
       for (uint32_t li = 0; li < ln; li += PAIRS) {
@@ -1186,7 +1219,7 @@ __global__ void __launch_bounds__(256, 4) k_binary_c(CacheView cv, BinaryPlan pl
         if (np == 0) break;  // rows ascend: no later row pairs with b either
         gen.a_rows = s_left + li * 32;
         const uint32_t en = en_ops & (np >= 8u ? 0xFFFFFFFFu : ((1u << (4 * np)) - 1u));
-        P::batch(cv, k, gen, int(4 * np), en, stage, pend, idr);
+        P::template batch<true>(cv, k, gen, int(4 * np), en, stage, pend, idr);
         built += __popc(en);
       }
     }
@@ -1223,9 +1256,12 @@ __global__ void __launch_bounds__(256, 4) k_desc_c(CacheView cv, const unsigned 
   for (uint32_t base = warp * N; base < n; base += nwarps * N) {
     if (__any_sync(kFull, stop_requested(cv))) break;
     const uint32_t cnt = min(uint32_t(N), n - base);
+    // descriptors past cnt (up to a multiple of 4) are harmless atoms, disabled by `en`
     if (lane < int(cnt)) dbuf[lane] = list ? list[base + lane] : pack_desc(kAtom, base + lane, 0);
+    else dbuf[lane] = pack_desc(kAtom, 0, 0);
     __syncwarp();
-    P::batch(cv, k, gen, int(cnt), cnt >= 32u ? 0xFFFFFFFFu : ((1u << cnt) - 1u), stage, pend, idr);
+    P::template batch<false>(cv, k, gen, int((cnt + 3u) & ~3u), cnt >= 32u ? 0xFFFFFFFFu : ((1u << cnt) - 1u),
+                             stage, pend, idr);
     __syncwarp();
   }
   PathB<W, 1>::flush(pend);

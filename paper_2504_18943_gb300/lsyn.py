@@ -53,7 +53,8 @@ class lsyn_level_stats(ctypes.Structure):
                 ("early_exit", ctypes.c_int32), ("candidates", ctypes.c_int64), ("unique", ctypes.c_int64),
                 ("total", ctypes.c_int64), ("deferred", ctypes.c_int64), ("ms", ctypes.c_double),
                 ("kernel_ms", ctypes.c_double * 4), ("bytes_alg", ctypes.c_double),
-                ("bytes_binary", ctypes.c_double), ("launches", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("bytes_binary", ctypes.c_double), ("bytes_unary", ctypes.c_double), ("launches", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("kernel_ms", "reserved")}
