@@ -467,8 +467,10 @@ lsyn_status lsyn_create(const lsyn_problem* problem, const lsyn_config* config, 
     unsigned rv = 1;
     while (32 * rv < L.vecs_needed) rv <<= 1;
     vecs = 32 * rv;
+  } else if (L.vecs_needed <= 4096) {
+    vecs = (L.vecs_needed + 31u) / 32u * 32u;  // path D: whole warps of vectors
   } else {
-    g_create_error = "characteristic matrices above 4 KiB (" + std::to_string(L.vecs_needed * 16) +
+    g_create_error = "characteristic matrices above 64 KiB (" + std::to_string(L.vecs_needed * 16) +
                      " bytes) are not supported by this build";
     return LSYN_E_UNSUPPORTED;
   }
@@ -502,7 +504,7 @@ lsyn_status lsyn_create(const lsyn_problem* problem, const lsyn_config* config, 
   c->max_len = L.max_len;
   c->steps = L.steps;
   c->vecs = vecs;
-  c->path = L.vecs_needed <= 8 ? 1 : 2;
+  c->path = L.vecs_needed <= 8 ? 1 : L.vecs_needed <= 256 ? 2 : 3;
   c->table_cap = best_cap;
   c->max_entries = unsigned(best_e);
   c->defer_cap = unsigned(std::max(1ull << 16, std::min(1ull << 23, best_e / 16)));

@@ -1270,6 +1270,304 @@ __global__ void __launch_bounds__(256, 4) k_desc_c(CacheView cv, const unsigned 
 }
 
 // ===========================================================================
+// Path D (CMs above 4 KiB, e.g. 2048 traces of 64-bit words = 16 KiB): the
+// hash-first scheme of path C with rv = vecs / 32 vectors per lane, walked in
+// loops. Operand rows are read through L1/L2 whenever a candidate is
+// (re)computed; compares read the stored row directly.
+// ===========================================================================
+template <typename W>
+struct PathD {
+  using Pending = typename PathB<W, 1>::Pending;
+  using Ids = typename PathB<W, 1>::Ids;
+
+  template <bool kEarlyPublish, class Gen>
+  __device__ static void batch(const CacheView& cv, const Gen& gen, int n, uint32_t en, Pending& pend, Ids& ids) {
+    const int lane = threadIdx.x & 31;
+    const unsigned rv = cv.vecs >> 5;
+    uint32_t my_lo = 0, my_hi = 0, bad = 0;
+    for (int q = 0; q < n; ++q) {
+      uint64_t acc = 0;
+      uint32_t diff = 0;
+      for (unsigned r = 0; r < rv; ++r) {
+        const unsigned v = lane + 32u * r;
+        const uint4 c = gen.compute(q, v);
+        acc = h_mac(c, __ldg(cv.hmul + v), acc);
+        diff |= bit0s<W>(c) ^ bit0s<W>(__ldg(cv.label + v));
+      }
+      const uint32_t lo = __reduce_add_sync(kFull, uint32_t(acc));
+      const uint32_t hi = __reduce_add_sync(kFull, uint32_t(acc >> 32));
+      my_lo = lane == q ? lo : my_lo;
+      my_hi = lane == q ? hi : my_hi;
+      bad |= (diff != 0u ? 1u : 0u) << q;
+    }
+    bad = __reduce_or_sync(kFull, bad);
+    const bool mine = lane < n && ((en >> lane) & 1u);
+    const uint64_t my_desc = gen.desc(lane < n ? lane : 0);
+    if (mine && !((bad >> lane) & 1u)) record_solution(cv, my_desc);
+
+    constexpr int kProbing = PathB<W, 1>::kProbing, kDone = PathB<W, 1>::kDone,
+                  kClaimed = PathB<W, 1>::kClaimed, kDeferred = PathB<W, 1>::kDeferred;
+    int state = mine ? kProbing : kDone;
+    const uint64_t h = h_fin(my_hi, my_lo);
+    const unsigned long long tag = (h >> 32) << 32;
+    unsigned long long pos = h & cv.table_mask;
+    // in-batch twins (equal hashes): settle them by comparing the candidates
+    const uint32_t mine_mask = __ballot_sync(kFull, mine);
+    const uint32_t peers = __match_any_sync(kFull, (unsigned long long)h) & mine_mask;
+    const bool has_twin = mine && (peers & ((1u << lane) - 1u)) != 0u;
+    const int twin = __ffs(peers) - 1;
+    for (uint32_t m = __ballot_sync(kFull, has_twin); m; m &= m - 1u) {
+      const int q = __ffs(m) - 1;
+      const int p = __shfl_sync(kFull, twin, q);
+      uint32_t ne = 0;
+      for (unsigned r = 0; r < rv; ++r) ne |= v_ne(gen.compute(q, lane + 32u * r), gen.compute(p, lane + 32u * r));
+      const bool eq = !__any_sync(kFull, ne != 0u);
+      if (lane == q && eq) state = kDone;
+    }
+    if (kEarlyPublish) PathB<W, 1>::flush(pend);
+    uint32_t cmp_id = 0;
+    unsigned long long guard = 0;
+    while (true) {
+      bool need = false;
+      if (state == kProbing) {
+        const unsigned long long sv = atomicCAS(cv.table + pos, 0ull, tag | kSlotPending);
+        if (sv == 0ull) {
+          state = kClaimed;
+        } else {
+          const uint32_t low = uint32_t(sv);
+          if ((sv & 0xFFFFFFFF00000000ull) != tag || low == kSlotTomb) pos = (pos + 1) & cv.table_mask;
+          else if (low == kSlotPending) state = kDeferred;
+          else {
+            need = true;
+            cmp_id = low - 1u;
+          }
+        }
+      }
+      for (uint32_t m = __ballot_sync(kFull, need); m; m &= m - 1u) {
+        const int q = __ffs(m) - 1;
+        const uint32_t id = __shfl_sync(kFull, cmp_id, q);
+        const uint4* src = row_ptr(cv, id);  // published: visible in L2, read past L1
+        uint32_t ne = 0;
+        for (unsigned r = 0; r < rv; ++r) ne |= v_ne(__ldcg(src + lane + 32u * r), gen.compute(q, lane + 32u * r));
+        const bool eq = !__any_sync(kFull, ne != 0u);
+        if (lane == q) {
+          if (eq) state = kDone;
+          else pos = (pos + 1) & cv.table_mask;
+        }
+      }
+      if (!__any_sync(kFull, state == kProbing)) break;
+      if (++guard > cv.table_mask) {
+        if (lane == 0) atomicExch(&cv.ctr->error, 1u);
+        if (state == kProbing) state = kDone;
+      }
+    }
+    const uint32_t claim = __ballot_sync(kFull, state == kClaimed);
+    const unsigned n_claim = unsigned(__popc(claim));
+    const unsigned have = ids.end - ids.next;
+    unsigned base = 0;
+    if (n_claim > have && lane == 0) base = atomicAdd(&cv.ctr->n_entries, max(cv.chunk, n_claim - have));
+    if (!kEarlyPublish) PathB<W, 1>::flush(pend);
+    if (claim) {
+      unsigned fresh = 0;
+      if (n_claim > have) fresh = __shfl_sync(kFull, base, 0);
+      unsigned rank = 0;
+      for (uint32_t m = claim; m; m &= m - 1u, ++rank) {
+        const int q = __ffs(m) - 1;
+        const unsigned id = rank < have ? ids.next + rank : fresh + (rank - have);
+        if (id < cv.max_entries) {
+          uint4* dst = cv.arena + size_t(id) * cv.vecs;
+          for (unsigned r = 0; r < rv; ++r) dst[lane + 32u * r] = gen.compute(q, lane + 32u * r);
+        }
+      }
+      const unsigned my_rank = unsigned(__popc(claim & ((1u << lane) - 1u)));
+      const unsigned my_id = my_rank < have ? ids.next + my_rank : fresh + (my_rank - have);
+      if (n_claim > have) {
+        ids.next = fresh + (n_claim - have);
+        ids.end = fresh + max(cv.chunk, n_claim - have);
+      } else {
+        ids.next += n_claim;
+      }
+      ids.inserted += n_claim;
+      if (state == kClaimed) {
+        unsigned long long* slot = cv.table + pos;
+        if (my_id < cv.max_entries) {
+          cv.prov[my_id] = my_desc;
+          cv.slotpos[my_id] = unsigned(pos);
+          pend.slot = slot;
+          pend.val = tag | (unsigned long long)(my_id + 1u);
+        } else {
+          st_relaxed(slot, tag | kSlotTomb);
+          atomicExch(&cv.ctr->full, 1u);
+        }
+      }
+    }
+    if (state == kDeferred) defer(cv, my_desc);
+  }
+};
+
+// Generators of path D: candidate q (0..31) from operand ids held in shared
+// memory (8 groups of 4 operators), vector v of this lane.
+template <typename W>
+struct PairGenD {
+  const CacheView* cv;
+  const uint2* pairs;  // shared memory: (a id, b id) of pair p
+  __device__ uint4 compute(int q, unsigned v) const {
+    const uint2 pr = pairs[q >> 2];
+    const uint4 a = __ldg(row_ptr(*cv, pr.x) + v), b = __ldg(row_ptr(*cv, pr.y) + v);
+    switch (q & 3) {
+      case 0: return v_op<W>(kAnd, a, b, b, 0);
+      case 1: return v_op<W>(kOr, a, b, b, 0);
+      case 2: return v_op<W>(kUntil, a, b, b, 0);
+      default: return v_op<W>(kUntil, b, a, b, 0);
+    }
+  }
+  __device__ uint64_t desc(int q) const {
+    const uint2 pr = pairs[q >> 2];
+    switch (q & 3) {
+      case 0: return pack_desc(kAnd, pr.x, pr.y);
+      case 1: return pack_desc(kOr, pr.x, pr.y);
+      case 2: return pack_desc(kUntil, pr.x, pr.y);
+      default: return pack_desc(kUntil, pr.y, pr.x);
+    }
+  }
+};
+
+template <typename W>
+struct RowGenD {
+  const CacheView* cv;
+  uint32_t id0;
+  __device__ uint4 compute(int q, unsigned v) const {
+    const uint4 a = __ldg(row_ptr(*cv, id0 + uint32_t(q >> 2)) + v);
+    return v_op<W>(unary_code(q & 3), a, a, __ldg(cv->lenmask + v), 0);
+  }
+  __device__ uint64_t desc(int q) const { return pack_desc(unary_code(q & 3), id0 + uint32_t(q >> 2), 0); }
+};
+
+template <typename W>
+struct ListGenD {
+  const CacheView* cv;
+  const uint64_t* d;  // shared memory: the batch's descriptors
+  __device__ uint4 compute(int q, unsigned v) const {
+    const uint64_t dd = d[q];
+    const uint32_t op = desc_op(dd);
+    if (op == kAtom) return __ldg(cv->atoms + size_t(desc_left(dd)) * cv->vecs + v);
+    const uint4 a = __ldg(row_ptr(*cv, desc_left(dd)) + v);
+    const uint4 b = (op == kAnd || op == kOr || op == kUntil) ? __ldg(row_ptr(*cv, desc_right(dd)) + v) : a;
+    return v_op<W>(op, a, b, __ldg(cv->lenmask + v), 0);
+  }
+  __device__ uint64_t desc(int q) const { return d[q]; }
+};
+
+template <typename W>
+__global__ void __launch_bounds__(256) k_unary_d(CacheView cv, uint32_t first, uint32_t count, uint32_t ops) {
+  using P = PathD<W>;
+  constexpr int ROWS = 8;
+  const int lane = threadIdx.x & 31;
+  RowGenD<W> gen;
+  gen.cv = &cv;
+  uint32_t en_ops = 0;
+#pragma unroll
+  for (int q = 0; q < 4 * ROWS; ++q) en_ops |= ((ops >> (q & 3)) & 1u) << q;
+  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  unsigned long long built = 0;
+  typename P::Pending pend;
+  typename P::Ids idr;
+  for (uint32_t base = warp * ROWS; base < count; base += nwarps * ROWS) {
+    if (__any_sync(kFull, stop_requested(cv))) break;
+    const uint32_t nrows = min(uint32_t(ROWS), count - base);
+    gen.id0 = first + base;
+    const uint32_t en = en_ops & (nrows >= 8u ? 0xFFFFFFFFu : ((1u << (4 * nrows)) - 1u));
+    P::template batch<false>(cv, gen, int(4 * nrows), en, pend, idr);
+    built += __popc(en);
+  }
+  PathB<W, 1>::flush(pend);
+  PathB<W, 1>::retire(cv, idr);
+  if (lane == 0 && built) atomicAdd(&cv.ctr->built, built);
+}
+
+// Pairs of every split in one flat index space (as path A), 8 per warp batch.
+template <typename W>
+__global__ void __launch_bounds__(256) k_binary_d(CacheView cv, BinaryPlan plan) {
+  using P = PathD<W>;
+  __shared__ uint2 s_pairs[8][8];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  PairGenD<W> gen;
+  gen.cv = &cv;
+  gen.pairs = s_pairs[wib];
+  const unsigned long long warp = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
+  const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+  unsigned long long built = 0;
+  typename P::Pending pend;
+  typename P::Ids idr;
+  for (unsigned long long g0 = warp * 8; g0 < plan.total_pairs; g0 += nwarps * 8) {
+    if (__any_sync(kFull, stop_requested(cv))) break;
+    // lane p < 8 maps pair g0 + p to its operands
+    uint32_t ok = 0;
+    if (lane < 8) {
+      const unsigned long long pidx = g0 + lane;
+      bool valid = pidx < plan.total_pairs;
+      uint2 pr = make_uint2(0, 0);
+      if (valid) {
+        int sp = 0;
+        while (sp + 1 < plan.n_splits && plan.s[sp + 1].pairs_begin <= pidx) ++sp;
+        const Split& S = plan.s[sp];
+        const unsigned long long local = pidx - S.pairs_begin;
+        const uint32_t ia = uint32_t(local / S.right_n);
+        const uint32_t ib = uint32_t(local - (unsigned long long)ia * S.right_n);
+        valid = !(S.tri && ia >= ib);
+        pr = make_uint2(S.left_start + ia, S.right_start + ib);
+      }
+      s_pairs[wib][lane] = pr;
+      ok = valid ? 1u : 0u;
+    }
+    const uint32_t pv = __ballot_sync(kFull, ok != 0u) & 0xFFu;
+    __syncwarp();
+    uint32_t en = 0;
+#pragma unroll
+    for (int q = 0; q < 32; ++q) en |= (((pv >> (q >> 2)) & 1u) & ((plan.ops >> (q & 3)) & 1u)) << q;
+    if (en) {
+      P::template batch<true>(cv, gen, 32, en, pend, idr);
+      built += __popc(en);
+    }
+    __syncwarp();
+  }
+  PathB<W, 1>::flush(pend);
+  PathB<W, 1>::retire(cv, idr);
+  if (lane == 0 && built) atomicAdd(&cv.ctr->built, built);
+}
+
+template <typename W>
+__global__ void __launch_bounds__(256) k_desc_d(CacheView cv, const unsigned long long* list,
+                                                const unsigned int* list_n, unsigned int list_cap,
+                                                unsigned int implicit_atoms) {
+  using P = PathD<W>;
+  __shared__ uint64_t s_d[8][32];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  ListGenD<W> gen;
+  gen.cv = &cv;
+  gen.d = s_d[wib];
+  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  unsigned n = implicit_atoms;
+  if (list) n = min(*list_n, list_cap);
+  typename P::Pending pend;
+  typename P::Ids idr;
+  for (uint32_t base = warp * 32; base < n; base += nwarps * 32) {
+    if (__any_sync(kFull, stop_requested(cv))) break;
+    const uint32_t cnt = min(32u, n - base);
+    s_d[wib][lane] = lane < int(cnt) ? (list ? list[base + lane] : pack_desc(kAtom, base + lane, 0))
+                                     : pack_desc(kAtom, 0, 0);
+    __syncwarp();
+    P::template batch<false>(cv, gen, int(cnt), cnt >= 32u ? 0xFFFFFFFFu : ((1u << cnt) - 1u), pend, idr);
+    __syncwarp();
+  }
+  PathB<W, 1>::flush(pend);
+  PathB<W, 1>::retire(cv, idr);
+  if (implicit_atoms && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&cv.ctr->built, (unsigned long long)n);
+}
+
+// ===========================================================================
 // Hole fixup: after a level, move the entries that lie above the level's dense
 // end into the holes below it (one warp per move): copy the CM row, its
 // provenance and slot index, and repoint the table slot to the new id.
@@ -1419,6 +1717,30 @@ struct LaunchC {
 };
 
 template <typename W>
+struct LaunchD {
+  static cudaError_t desc_list(const CacheView& cv, const unsigned long long* list, const unsigned int* list_n,
+                               unsigned int cap, unsigned int atoms, const LaunchCfg& lc) {
+    const unsigned n = list ? cap : atoms;
+    const unsigned blocks = std::max(1u, std::min((n + 255u) / 256u, unsigned(lc.sms * 8)));
+    k_desc_d<W><<<blocks, 256, 0, lc.stream>>>(cv, list, list_n, cap, atoms);
+    return cudaGetLastError();
+  }
+  static cudaError_t unary(const CacheView& cv, uint32_t first, uint32_t count, uint32_t ops, const LaunchCfg& lc) {
+    static int occ = occupancy_blocks((const void*)k_unary_d<W>, 256, 0);
+    const unsigned blocks = std::max(1u, std::min((count + 63u) / 64u, unsigned(lc.sms * occ)));
+    k_unary_d<W><<<blocks, 256, 0, lc.stream>>>(cv, first, count, ops);
+    return cudaGetLastError();
+  }
+  static cudaError_t binary(const CacheView& cv, const BinaryPlan& plan, const LaunchCfg& lc) {
+    static int occ = occupancy_blocks((const void*)k_binary_d<W>, 256, 0);
+    const unsigned long long want = (plan.total_pairs + 63ull) / 64ull;
+    const unsigned blocks = unsigned(std::max(1ull, std::min(want, (unsigned long long)lc.sms * occ)));
+    k_binary_d<W><<<blocks, 256, 0, lc.stream>>>(cv, plan);
+    return cudaGetLastError();
+  }
+};
+
+template <typename W>
 int Kernels<W>::path_for(unsigned vecs) {
   if (vecs == 1 || vecs == 2 || vecs == 4 || vecs == 8) return 1;
   if (vecs == 32 || vecs == 64 || vecs == 128 || vecs == 256) return 2;
@@ -1435,7 +1757,9 @@ int Kernels<W>::path_for(unsigned vecs) {
     case 64: return LaunchB<W, 2>::CALL_B;              \
     case 128: return LaunchB<W, 4>::CALL_B;             \
     case 256: return LaunchB<W, 8>::CALL_B;             \
-    default: return cudaErrorInvalidValue;              \
+    default:                                            \
+      if (vecs > 256 && vecs % 32 == 0) return LaunchD<W>::CALL_B; \
+      return cudaErrorInvalidValue;                     \
   }
 
 template <typename W>

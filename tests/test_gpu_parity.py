@@ -274,8 +274,41 @@ def test_torch_allocator_and_stream(L):
     assert_levels_match(L, p, 6, config=cfg)
 
 
-def test_large_matrices_unsupported_yet(L):
-    p = _random_problem(13, 2, 300, 300, 4, 8, 64)  # 4800-byte matrices
+def test_wide_matrices_path(L):
+    """CMs above 4 KiB (600 traces of 64-bit words = 4800 bytes) take the loop-per-lane path."""
+    assert_levels_match(L, _random_problem(13, 2, 300, 300, 4, 8, 64), 4)
+
+
+def test_matrices_above_64k_unsupported(L):
+    p = _random_problem(14, 1, 4200, 4200, 2, 3, 64)  # 67200 bytes
     with pytest.raises(L.LsynError) as ei:
         L.Synthesizer(L.pack_problem(p))
     assert ei.value.status == L.LSYN_E_UNSUPPORTED
+
+
+def test_large_workload_full_size(L):
+    """The large configuration (10 propositions, 1024 + 1024 traces of length
+    16..64, 16 KiB CMs): levels 1..3 equal the oracle's; deeper entries are
+    sampled and re-evaluated one by one by the oracle; the run either solves
+    (minimal: every level below complete) or fills the cache."""
+    p = W.large_problem(0, oracle.labeller)
+    assert p.n_traces == 2048 and p.word_bits == 64
+    spec = oracle.Spec.from_problem(p)
+    assert_levels_match(L, p, 3, cache_bytes=2 << 30, spec=spec)
+    packed = L.pack_problem(p)
+    with L.Synthesizer(packed, L.torch_config(cache_bytes=24 << 30)) as s:
+        st, res, f, levels = s.solve(15)
+        assert st in (L.LSYN_OK, L.LSYN_E_CACHE_FULL), L.lsyn_last_error(s.ctx)
+        if st == L.LSYN_OK:
+            assert spec.separates(f) and W.formula_size(f) == res.size
+        else:
+            assert levels[-1].cache_full == 1 and res.found == 0
+        rng = np.random.default_rng(0)
+        for k in range(1, res.levels_done + 1):
+            n = s.count(k)
+            rows = s.export(k, 0, min(n, 4000))
+            assert canon(rows).shape[0] == rows.shape[0], f"duplicates in level {k}"
+            for idx in rng.choice(n, size=min(n, 4), replace=False):
+                f_k = s.formula(k, int(idx))
+                cm = oracle_rows([spec.eval(f_k)], 64, p.n_traces)[0]
+                assert np.array_equal(cm, s.export(k, int(idx), 1)[0]) and W.formula_size(f_k) == k
