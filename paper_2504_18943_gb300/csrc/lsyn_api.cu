@@ -459,16 +459,15 @@ lsyn_status lsyn_create(const lsyn_problem* problem, const lsyn_config* config, 
   if (!(load > 0 && load <= 0.9)) { g_create_error = "table_load must be in (0, 0.9]"; return LSYN_E_INVAL; }
   const unsigned long long cache_bytes = cfg.cache_bytes ? cfg.cache_bytes : (1ull << 30);
 
+  // Paths: A (thread per candidate) up to 128 bytes, padded to a power of two
+  // of 16-byte vectors; C (one vector per lane) up to 512 bytes; D (whole
+  // warps of vectors, looped per lane) up to 64 KiB.
   unsigned vecs = 0;
   if (L.vecs_needed <= 8) {
     vecs = 1;
     while (vecs < L.vecs_needed) vecs <<= 1;
-  } else if (L.vecs_needed <= 256) {
-    unsigned rv = 1;
-    while (32 * rv < L.vecs_needed) rv <<= 1;
-    vecs = 32 * rv;
   } else if (L.vecs_needed <= 4096) {
-    vecs = (L.vecs_needed + 31u) / 32u * 32u;  // path D: whole warps of vectors
+    vecs = (L.vecs_needed + 31u) / 32u * 32u;
   } else {
     g_create_error = "characteristic matrices above 64 KiB (" + std::to_string(L.vecs_needed * 16) +
                      " bytes) are not supported by this build";
@@ -504,7 +503,7 @@ lsyn_status lsyn_create(const lsyn_problem* problem, const lsyn_config* config, 
   c->max_len = L.max_len;
   c->steps = L.steps;
   c->vecs = vecs;
-  c->path = L.vecs_needed <= 8 ? 1 : L.vecs_needed <= 256 ? 2 : 3;
+  c->path = L.vecs_needed <= 8 ? 1 : vecs == 32 ? 2 : 3;
   c->table_cap = best_cap;
   c->max_entries = unsigned(best_e);
   c->defer_cap = unsigned(std::max(1ull << 16, std::min(1ull << 23, best_e / 16)));

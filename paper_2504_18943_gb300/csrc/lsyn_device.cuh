@@ -238,7 +238,9 @@ struct PathA {
   }
 
   // Spec check, then probe / compare / insert one candidate.
-  __device__ static unsigned process(const CacheView& cv, const Consts& s, const uint4 (&c)[V], uint64_t desc) {
+  // `full`: the arena is full, so only the spec check is done (see path C).
+  __device__ static unsigned process(const CacheView& cv, const Consts& s, const uint4 (&c)[V], uint64_t desc,
+                                     bool full) {
     uint32_t lo = 0, hi = 0, bad = 0;
 #pragma unroll
     for (int v = 0; v < V; ++v) {
@@ -246,6 +248,7 @@ struct PathA {
       bad |= spec_bad(c[v], s.lab[v], s.care[v]);
     }
     if (bad == 0) record_solution(cv, desc);
+    if (full) return 0;
     const uint64_t h = h_fin(hi, lo);
     const unsigned long long tag = (h >> 32) << 32;
     unsigned long long pos = h & cv.table_mask;
@@ -283,11 +286,11 @@ struct PathA {
   }
 
   __device__ static unsigned candidate(const CacheView& cv, const Consts& s, uint32_t op, const uint4 (&a)[V],
-                                       const uint4 (&b)[V], uint64_t desc) {
+                                       const uint4 (&b)[V], uint64_t desc, bool full) {
     uint4 c[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) c[v] = v_op<W>(op, a[v], b[v], s.lm[v], cv.steps);
-    return process(cv, s, c, desc);
+    return process(cv, s, c, desc, full);
   }
 };
 
@@ -301,6 +304,7 @@ __global__ void __launch_bounds__(256) k_unary_a(CacheView cv, uint32_t first, u
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
     if (stop_requested(cv)) break;
+    const bool full = ld_relaxed_u32(&cv.ctr->full) != 0u;
     const uint32_t id = first + i;
     uint4 a[V];
     P::load_row(row_ptr(cv, id), a);
@@ -308,7 +312,7 @@ __global__ void __launch_bounds__(256) k_unary_a(CacheView cv, uint32_t first, u
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       if (!((ops >> q) & 1u)) continue;
-      ins += P::candidate(cv, s, opc[q], a, a, pack_desc(opc[q], id, 0));
+      ins += P::candidate(cv, s, opc[q], a, a, pack_desc(opc[q], id, 0), full);
       ++built;
     }
   }
@@ -335,13 +339,14 @@ __global__ void __launch_bounds__(256) k_binary_a(CacheView cv, BinaryPlan plan)
     const uint32_t ib = uint32_t(local - (unsigned long long)ia * S.right_n);
     if (S.tri && ia >= ib) continue;  // same level: unordered pairs a < b only
     const uint32_t a_id = S.left_start + ia, b_id = S.right_start + ib;
+    const bool full = ld_relaxed_u32(&cv.ctr->full) != 0u;
     uint4 a[V], b[V];
     P::load_row(row_ptr(cv, a_id), a);
     P::load_row(row_ptr(cv, b_id), b);
-    if (plan.ops & 1u) { ins += P::candidate(cv, s, kAnd, a, b, pack_desc(kAnd, a_id, b_id)); ++built; }
-    if (plan.ops & 2u) { ins += P::candidate(cv, s, kOr, a, b, pack_desc(kOr, a_id, b_id)); ++built; }
-    if (plan.ops & 4u) { ins += P::candidate(cv, s, kUntil, a, b, pack_desc(kUntil, a_id, b_id)); ++built; }
-    if (plan.ops & 8u) { ins += P::candidate(cv, s, kUntil, b, a, pack_desc(kUntil, b_id, a_id)); ++built; }
+    if (plan.ops & 1u) { ins += P::candidate(cv, s, kAnd, a, b, pack_desc(kAnd, a_id, b_id), full); ++built; }
+    if (plan.ops & 2u) { ins += P::candidate(cv, s, kOr, a, b, pack_desc(kOr, a_id, b_id), full); ++built; }
+    if (plan.ops & 4u) { ins += P::candidate(cv, s, kUntil, a, b, pack_desc(kUntil, a_id, b_id), full); ++built; }
+    if (plan.ops & 8u) { ins += P::candidate(cv, s, kUntil, b, a, pack_desc(kUntil, b_id, a_id), full); ++built; }
   }
   if (built) atomicAdd(&cv.ctr->built, built);
   if (ins) atomicAdd(&cv.ctr->inserted, ins);
@@ -383,19 +388,14 @@ __global__ void __launch_bounds__(256) k_desc_a(CacheView cv, const unsigned lon
     const uint64_t d = list ? list[i] : pack_desc(kAtom, i, 0);
     uint4 c[V];
     rebuild_a<W, V>(cv, s, d, c);
-    ins += P::process(cv, s, c, d);
+    ins += P::process(cv, s, c, d, ld_relaxed_u32(&cv.ctr->full) != 0u);
   }
   if (ins) atomicAdd(&cv.ctr->inserted, ins);
   if (implicit_atoms && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&cv.ctr->built, (unsigned long long)n);
 }
 
 // ===========================================================================
-// Path B: a warp holds a CM; lane l holds vectors l, l + 32, ... (RV of them).
-// Candidates go through the dedup in batches of NB = 8 / RV, so that their
-// table probes (one CAS per probe, issued by lane q for candidate q) and their
-// compare reads are in flight together. Compare reads are staged into shared
-// memory with cp.async (L2-coherent, no registers held while in flight); a
-// batch's new CMs are written, fenced once, and published.
+// Warp paths (C and D): a warp holds a CM, lane l holds vectors l, l + 32, ...
 // ===========================================================================
 __device__ __forceinline__ void cp_async16(uint4* smem, const uint4* gmem) {
   const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
@@ -422,34 +422,9 @@ template <> __device__ __forceinline__ uint32_t bit0s<uint32_t>(uint4 c) {
 }
 template <> __device__ __forceinline__ uint32_t bit0s<uint64_t>(uint4 c) { return (c.y >> 31) | ((c.w >> 31) << 1); }
 
-template <typename W, int RV>
-struct PathB {
-  static constexpr int NB = 8 / RV;                  // candidates per batch
-  static constexpr int WPV = int(16 / sizeof(W));    // trace words per vector
-  static constexpr int kStage = NB * RV * 32;        // uint4 of compare staging per warp
-
-  struct LaneConsts {
-    uint4 mul[RV];  // hash multipliers of this lane's 32-bit words
-    uint32_t lab;   // bit (r * WPV + j): 1 iff word j of vector r belongs to a positive trace
-  };
-
-  __device__ static void load_consts(const CacheView& cv, LaneConsts& k) {
-    const int lane = threadIdx.x & 31;
-    k.lab = 0;
-#pragma unroll
-    for (int r = 0; r < RV; ++r) {
-      const int v = lane + 32 * r;
-      k.mul[r] = cv.hmul[v];
-      k.lab |= bit0s<W>(cv.label[v]) << (r * WPV);
-    }
-  }
-
-  __device__ static void load_row(const uint4* p, uint4 (&x)[RV]) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int r = 0; r < RV; ++r) x[r] = __ldg(p + lane + 32 * r);
-  }
-
+// Warp-batch bookkeeping shared by paths C and D: probe states, pending
+// publication of claimed slots, and per-warp id reservations.
+struct WarpDedup {
   enum { kProbing = 0, kDone = 1, kClaimed = 2, kDeferred = 3 };
 
   // Ids this warp reserved from the shared counter and has not used yet:
@@ -476,10 +451,8 @@ struct PathB {
   }
 
   // A slot this lane claimed whose CM words were stored but not yet
-  // published. It is published by the next batch (or by flush()), after a
-  // fence that by then no longer waits for those stores: the fence is off the
-  // critical path. Meanwhile the slot reads as pending and an equal candidate
-  // is deferred.
+  // published. It is published by a later batch (or by flush()) after a fence;
+  // meanwhile the slot reads as pending and an equal candidate is deferred.
   struct Pending {
     unsigned long long* slot = nullptr;
     unsigned long long val = 0;
@@ -494,361 +467,10 @@ struct PathB {
       pend.slot = nullptr;
     }
   }
-
-  // Spec check, probe, compare and insert a batch of NB candidates. Every lane
-  // holds its slices c[q][*] of every candidate q; lane q (q < NB) also holds
-  // the descriptor of candidate q. Bit q of `en` (warp-uniform) says candidate
-  // q is real. `stage` is this warp's kStage uint4 of shared memory.
-  __device__ static void batch(const CacheView& cv, const LaneConsts& k, const uint4 (&c)[NB][RV],
-                               uint64_t my_desc, uint32_t en, uint4* stage, Pending& pend, Ids& ids) {
-    const int lane = threadIdx.x & 31;
-    uint32_t my_lo = 0, my_hi = 0, bad = 0;
-#pragma unroll
-    for (int q = 0; q < NB; ++q) {
-      uint64_t acc = 0;
-      uint32_t bits = 0;
-#pragma unroll
-      for (int r = 0; r < RV; ++r) {
-        acc = h_mac(c[q][r], k.mul[r], acc);
-        bits |= bit0s<W>(c[q][r]) << (r * WPV);
-      }
-      const uint32_t lo = __reduce_add_sync(kFull, uint32_t(acc));
-      const uint32_t hi = __reduce_add_sync(kFull, uint32_t(acc >> 32));
-      my_lo = lane == q ? lo : my_lo;
-      my_hi = lane == q ? hi : my_hi;
-      bad |= ((bits ^ k.lab) != 0u ? 1u : 0u) << q;
-    }
-    // Separation (section "Synthesising ... from examples"): the position-0 bit
-    // of every trace word equals the trace's label. Padding words are 0 with
-    // label 0.
-    bad = __reduce_or_sync(kFull, bad);
-    const bool mine = lane < NB && ((en >> lane) & 1u);
-    if (mine && !((bad >> lane) & 1u)) record_solution(cv, my_desc);
-
-    int state = mine ? kProbing : kDone;
-    const uint64_t h = h_fin(my_hi, my_lo);
-    const unsigned long long tag = (h >> 32) << 32;
-    unsigned long long pos = h & cv.table_mask;
-    uint32_t cmp_id = 0;
-    unsigned long long guard = 0;
-    while (true) {
-      bool need = false;
-      if (state == kProbing) {
-        // One atomic per probe: claims an empty slot, or returns what is there.
-        const unsigned long long sv = atomicCAS(cv.table + pos, 0ull, tag | kSlotPending);
-        if (sv == 0ull) {
-          state = kClaimed;
-        } else {
-          const uint32_t low = uint32_t(sv);
-          if ((sv & 0xFFFFFFFF00000000ull) != tag || low == kSlotTomb) pos = (pos + 1) & cv.table_mask;
-          else if (low == kSlotPending) state = kDeferred;
-          else {
-            need = true;
-            cmp_id = low - 1u;
-          }
-        }
-      }
-      const uint32_t cm = __ballot_sync(kFull, need);
-      if (cm) {
-        // The published entry's CM was made visible in L2 before its slot
-        // (writer's fence); cp.async.cg reads it from L2.
-#pragma unroll
-        for (int q = 0; q < NB; ++q) {
-          const uint32_t id = __shfl_sync(kFull, cmp_id, q);
-          if ((cm >> q) & 1u) {
-            const uint4* src = row_ptr(cv, id);
-#pragma unroll
-            for (int r = 0; r < RV; ++r) cp_async16(stage + (q * RV + r) * 32 + lane, src + lane + 32 * r);
-          }
-        }
-        cp_async_wait_all();
-        uint32_t ne = 0;
-#pragma unroll
-        for (int q = 0; q < NB; ++q) {
-          uint32_t d = 0;
-          if ((cm >> q) & 1u) {
-#pragma unroll
-            for (int r = 0; r < RV; ++r) d |= v_ne(stage[(q * RV + r) * 32 + lane], c[q][r]);
-          }
-          ne |= (d != 0u ? 1u : 0u) << q;
-        }
-        ne = __reduce_or_sync(kFull, ne);
-        if (need) {
-          if (!((ne >> lane) & 1u)) state = kDone;  // equal CM already cached
-          else pos = (pos + 1) & cv.table_mask;
-        }
-      }
-      if (!__any_sync(kFull, state == kProbing)) break;
-      if (++guard > cv.table_mask) {  // every slot seen: cannot happen at load <= 0.9
-        if (lane == 0) atomicExch(&cv.ctr->error, 1u);
-        if (state == kProbing) state = kDone;
-      }
-    }
-
-    const uint32_t claim = __ballot_sync(kFull, state == kClaimed);
-    const unsigned n_claim = unsigned(__popc(claim));
-    const unsigned have = ids.end - ids.next;  // warp-uniform
-    unsigned base = 0;
-    if (n_claim > have && lane == 0) base = atomicAdd(&cv.ctr->n_entries, max(cv.chunk, n_claim - have));
-    flush(pend);  // the previous batch's slots; overlaps the id reservation above
-    if (claim) {
-      // Ids of the claimed candidates in lane order: first what is left of the
-      // current reservation, then a fresh one.
-      unsigned fresh = 0;
-      if (n_claim > have) {
-        fresh = __shfl_sync(kFull, base, 0);
-      }
-      auto id_of = [&](unsigned rank) { return rank < have ? ids.next + rank : fresh + (rank - have); };
-#pragma unroll
-      for (int q = 0; q < NB; ++q) {
-        if (!((claim >> q) & 1u)) continue;
-        const unsigned id = id_of(unsigned(__popc(claim & ((1u << q) - 1u))));
-        if (id < cv.max_entries) {
-          uint4* dst = cv.arena + size_t(id) * cv.vecs;
-#pragma unroll
-          for (int r = 0; r < RV; ++r) dst[lane + 32 * r] = c[q][r];
-        }
-      }
-      const unsigned my_id = id_of(unsigned(__popc(claim & ((1u << lane) - 1u))));
-      if (n_claim > have) {
-        ids.next = fresh + (n_claim - have);
-        ids.end = fresh + max(cv.chunk, n_claim - have);
-      } else {
-        ids.next += n_claim;
-      }
-      ids.inserted += n_claim;
-      if (state == kClaimed) {
-        unsigned long long* slot = cv.table + pos;
-        if (my_id < cv.max_entries) {
-          cv.prov[my_id] = my_desc;
-          cv.slotpos[my_id] = unsigned(pos);
-          pend.slot = slot;
-          pend.val = tag | (unsigned long long)(my_id + 1u);
-        } else {
-          st_relaxed(slot, tag | kSlotTomb);  // nothing to order: no CM behind it
-          atomicExch(&cv.ctr->full, 1u);
-        }
-      }
-    }
-    if (state == kDeferred) defer(cv, my_desc);
-  }
 };
 
 // Unary operator code of position o in the batch order (not, X, F, G).
 __device__ __forceinline__ uint32_t unary_code(int o) { return o == 0 ? kNot : uint32_t(3 + o); }
-
-template <typename W, int RV>
-__global__ void __launch_bounds__(256, 3) k_unary_b(CacheView cv, uint32_t first, uint32_t count, uint32_t ops) {
-  using P = PathB<W, RV>;
-  constexpr int NB = P::NB;
-  constexpr int ROWS = NB >= 4 ? NB / 4 : 1;  // rows per batch group
-  constexpr int G = NB >= 4 ? 1 : 4 / NB;     // batches per row group
-  extern __shared__ uint4 smem[];
-  const int lane = threadIdx.x & 31;
-  uint4* stage = smem + (threadIdx.x >> 5) * P::kStage;
-  typename P::LaneConsts k;
-  P::load_consts(cv, k);
-  uint4 lm[RV];
-#pragma unroll
-  for (int r = 0; r < RV; ++r) lm[r] = cv.lenmask[lane + 32 * r];
-  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-  unsigned long long built = 0;
-  typename P::Pending pend;
-  typename P::Ids idr;
-  uint32_t iter = 0;
-  for (uint32_t base = warp * ROWS; base < count; base += nwarps * ROWS, ++iter) {
-    if ((iter & 3u) == 0 && __any_sync(kFull, stop_requested(cv))) break;
-    uint4 a[ROWS][RV];
-    uint32_t rows_ok = 0;
-#pragma unroll
-    for (int p = 0; p < ROWS; ++p) {
-      if (base + p < count) {
-        P::load_row(row_ptr(cv, first + base + p), a[p]);
-        rows_ok |= 1u << p;
-      } else {
-#pragma unroll
-        for (int r = 0; r < RV; ++r) a[p][r] = make_uint4(0, 0, 0, 0);
-      }
-    }
-#pragma unroll
-    for (int g = 0; g < G; ++g) {
-      uint4 c[NB][RV];
-      uint32_t en = 0;
-#pragma unroll
-      for (int j = 0; j < NB; ++j) {
-        const int flat = g * NB + j, p = flat / 4, o = flat % 4;
-#pragma unroll
-        for (int r = 0; r < RV; ++r) c[j][r] = v_op<W>(unary_code(o), a[p][r], a[p][r], lm[r], cv.steps);
-        if (((rows_ok >> p) & 1u) && ((ops >> o) & 1u)) en |= 1u << j;
-      }
-      const int flat = g * NB + lane;
-      const uint64_t my_desc = pack_desc(unary_code(flat & 3), first + base + uint32_t(flat >> 2), 0);
-      P::batch(cv, k, c, my_desc, en, stage, pend, idr);
-      built += __popc(en);
-    }
-  }
-  P::flush(pend);
-  P::retire(cv, idr);
-  if (lane == 0 && built) atomicAdd(&cv.ctr->built, built);
-}
-
-// Binary operators over tiles of a split: the CTA stages `tile` rows of the
-// smaller level in shared memory (amortising their loads over every row of the
-// other level, paragraph "Amortising the cost of data movement"), and each warp
-// streams rows of the other level through registers, building a & b, a | b,
-// a U b and b U a for every staged row a.
-template <typename W, int RV>
-__global__ void __launch_bounds__(256, 3) k_binary_b(CacheView cv, BinaryPlan plan) {
-  using P = PathB<W, RV>;
-  constexpr int NB = P::NB;
-  constexpr int PAIRS = NB >= 4 ? NB / 4 : 1;  // pairs per batch group
-  constexpr int G = NB >= 4 ? 1 : 4 / NB;      // batches per pair group
-  extern __shared__ uint4 smem[];
-  __shared__ unsigned long long s_tile;
-  const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
-  const int nwarps = blockDim.x >> 5;
-  const unsigned vecs = cv.vecs;
-  uint4* s_left = smem;
-  uint4* stage = smem + size_t(plan.tile) * vecs + warp * P::kStage;
-  typename P::LaneConsts k;
-  P::load_consts(cv, k);
-  const uint4 zero = make_uint4(0, 0, 0, 0);
-  unsigned long long built = 0;
-  typename P::Pending pend;
-  typename P::Ids idr;
-  while (true) {
-    if (threadIdx.x == 0) {
-      unsigned long long t = atomicAdd(&cv.ctr->work[plan.work_slot], 1ull);
-      if (stop_requested(cv)) t = plan.total_tiles;
-      s_tile = t;
-    }
-    __syncthreads();
-    const unsigned long long tile = s_tile;
-    if (tile >= plan.total_tiles) break;
-    int sp = 0;
-    while (sp + 1 < plan.n_splits && plan.s[sp + 1].tiles_begin <= tile) ++sp;
-    const Split& S = plan.s[sp];
-    const unsigned long long t = tile - S.tiles_begin;
-    const uint32_t lt = uint32_t(t / S.rt_tiles);
-    const uint32_t rt = uint32_t(t - (unsigned long long)lt * S.rt_tiles);
-    const bool skip = S.tri && rt < lt;
-    const uint32_t l0 = lt * plan.tile, r0 = rt * plan.tile;
-    const uint32_t ln = skip ? 0u : min(plan.tile, S.left_n - l0);
-    const uint32_t rn = skip ? 0u : min(plan.tile, S.right_n - r0);
-    {
-      const uint4* src = row_ptr(cv, S.left_start + l0);
-      const uint32_t total = ln * vecs;
-      for (uint32_t i = threadIdx.x; i < total; i += blockDim.x) s_left[i] = __ldg(src + i);
-    }
-    __syncthreads();
-    for (uint32_t rr = warp; rr < rn; rr += nwarps) {
-      if (__any_sync(kFull, stop_requested(cv))) break;
-      const uint32_t b_id = S.right_start + r0 + rr;
-      uint4 b[RV];
-      P::load_row(row_ptr(cv, b_id), b);
-      for (uint32_t li = 0; li < ln; li += PAIRS) {
-        uint4 a[PAIRS][RV];
-        const uint32_t a0 = S.left_start + l0 + li;
-        uint32_t pv = 0;
-#pragma unroll
-        for (int p = 0; p < PAIRS; ++p) {
-          const bool ok = li + p < ln && (!S.tri || a0 + p < b_id);
-          if (ok) pv |= 1u << p;
-#pragma unroll
-          for (int r = 0; r < RV; ++r) a[p][r] = ok ? s_left[(li + p) * vecs + lane + 32 * r] : zero;
-        }
-        if (!pv) break;  // rows ascend: no later row pairs with b either
-#pragma unroll
-        for (int g = 0; g < G; ++g) {
-          uint4 c[NB][RV];
-          uint32_t en = 0;
-#pragma unroll
-          for (int j = 0; j < NB; ++j) {
-            const int flat = g * NB + j, p = flat / 4, o = flat % 4;
-#pragma unroll
-            for (int r = 0; r < RV; ++r) {
-              if (o == 0) c[j][r] = v_op<W>(kAnd, a[p][r], b[r], b[r], cv.steps);
-              else if (o == 1) c[j][r] = v_op<W>(kOr, a[p][r], b[r], b[r], cv.steps);
-              else if (o == 2) c[j][r] = v_op<W>(kUntil, a[p][r], b[r], b[r], cv.steps);
-              else c[j][r] = v_op<W>(kUntil, b[r], a[p][r], b[r], cv.steps);
-            }
-            if (((pv >> p) & 1u) && ((plan.ops >> o) & 1u)) en |= 1u << j;
-          }
-          // lane q's candidate: pair q / 4 of the group, operator q % 4
-          const int flat = g * NB + lane, o = flat & 3;
-          const uint32_t ai = a0 + uint32_t(flat >> 2);
-          const uint64_t my_desc = o == 0 ? pack_desc(kAnd, ai, b_id)
-                                 : o == 1 ? pack_desc(kOr, ai, b_id)
-                                 : o == 2 ? pack_desc(kUntil, ai, b_id)
-                                          : pack_desc(kUntil, b_id, ai);
-          P::batch(cv, k, c, my_desc, en, stage, pend, idr);
-          built += __popc(en);
-        }
-      }
-    }
-    __syncthreads();
-  }
-  P::flush(pend);
-  P::retire(cv, idr);
-  if (lane == 0 && built) atomicAdd(&cv.ctr->built, built);
-}
-
-template <typename W, int RV>
-__global__ void __launch_bounds__(256, 3) k_desc_b(CacheView cv, const unsigned long long* list,
-                                                   const unsigned int* list_n, unsigned int list_cap,
-                                                   unsigned int implicit_atoms) {
-  using P = PathB<W, RV>;
-  constexpr int NB = P::NB;
-  extern __shared__ uint4 smem[];
-  const int lane = threadIdx.x & 31;
-  uint4* stage = smem + (threadIdx.x >> 5) * P::kStage;
-  typename P::LaneConsts k;
-  P::load_consts(cv, k);
-  uint4 lm[RV];
-#pragma unroll
-  for (int r = 0; r < RV; ++r) lm[r] = cv.lenmask[lane + 32 * r];
-  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-  unsigned n = implicit_atoms;
-  if (list) n = min(*list_n, list_cap);
-  typename P::Pending pend;
-  typename P::Ids idr;
-  for (uint32_t base = warp * NB; base < n; base += nwarps * NB) {
-    if (__any_sync(kFull, stop_requested(cv))) break;
-    uint4 c[NB][RV];
-    uint32_t en = 0;
-    uint64_t my_desc = 0;
-#pragma unroll
-    for (int j = 0; j < NB; ++j) {
-#pragma unroll
-      for (int r = 0; r < RV; ++r) c[j][r] = make_uint4(0, 0, 0, 0);
-      if (base + j >= n) continue;
-      en |= 1u << j;
-      const uint64_t d = list ? list[base + j] : pack_desc(kAtom, base + j, 0);
-      my_desc = lane == j ? d : my_desc;
-      const uint32_t op = desc_op(d);
-      if (op == kAtom) {
-        P::load_row(cv.atoms + size_t(desc_left(d)) * cv.vecs, c[j]);
-      } else {
-        uint4 a[RV], b[RV];
-        P::load_row(row_ptr(cv, desc_left(d)), a);
-        if (op == kAnd || op == kOr || op == kUntil) P::load_row(row_ptr(cv, desc_right(d)), b);
-        else {
-#pragma unroll
-          for (int r = 0; r < RV; ++r) b[r] = a[r];
-        }
-#pragma unroll
-        for (int r = 0; r < RV; ++r) c[j][r] = v_op<W>(op, a[r], b[r], lm[r], cv.steps);
-      }
-    }
-    P::batch(cv, k, c, my_desc, en, stage, pend, idr);
-  }
-  P::flush(pend);
-  P::retire(cv, idr);
-  if (implicit_atoms && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&cv.ctr->built, (unsigned long long)n);
-}
 
 // ===========================================================================
 // Path C (CMs of exactly one 16-byte vector per lane: 32 vectors, 512 bytes for
@@ -865,8 +487,8 @@ struct PathC {
   static constexpr int kGroup = 8;             // compare reads staged together
   static constexpr int kStage = kGroup * 32;   // uint4 of staging per warp
 
-  using Pending = typename PathB<W, 1>::Pending;
-  using Ids = typename PathB<W, 1>::Ids;
+  using Pending = WarpDedup::Pending;
+  using Ids = WarpDedup::Ids;
 
   struct Consts {
     uint4 mul;     // hash multipliers of this lane's 32-bit words
@@ -925,9 +547,13 @@ struct PathC {
     const uint64_t my_desc = gen.desc(lane < n ? lane : 0);
     if (mine && !((bad >> lane) & 1u)) record_solution(cv, my_desc);
 
-    int state = mine ? PathB<W, 1>::kProbing : PathB<W, 1>::kDone;
-    constexpr int kProbing = PathB<W, 1>::kProbing, kDone = PathB<W, 1>::kDone,
-                  kClaimed = PathB<W, 1>::kClaimed, kDeferred = PathB<W, 1>::kDeferred;
+    // Once the arena is full this level can never be extended: only the spec
+    // check (above) matters, so the rest of the batch skips the dedup instead
+    // of filling the table with tombstones.
+    const bool full = __any_sync(kFull, lane == 0 && ld_relaxed_u32(&cv.ctr->full) != 0u);
+    int state = (mine && !full) ? WarpDedup::kProbing : WarpDedup::kDone;
+    constexpr int kProbing = WarpDedup::kProbing, kDone = WarpDedup::kDone,
+                  kClaimed = WarpDedup::kClaimed, kDeferred = WarpDedup::kDeferred;
     const uint64_t h = h_fin(my_hi, my_lo);
     const unsigned long long tag = (h >> 32) << 32;
     unsigned long long pos = h & cv.table_mask;
@@ -946,7 +572,7 @@ struct PathC {
       if (lane == q && eq) state = kDone;
     }
 
-    if (kEarlyPublish) PathB<W, 1>::flush(pend);
+    if (kEarlyPublish) WarpDedup::flush(pend);
     uint32_t cmp_id = 0;
     unsigned long long guard = 0;
     while (true) {
@@ -1003,7 +629,7 @@ struct PathC {
     const unsigned have = ids.end - ids.next;  // warp-uniform
     unsigned base = 0;
     if (n_claim > have && lane == 0) base = atomicAdd(&cv.ctr->n_entries, max(cv.chunk, n_claim - have));
-    if (!kEarlyPublish) PathB<W, 1>::flush(pend);  // overlaps the id reservation above
+    if (!kEarlyPublish) WarpDedup::flush(pend);  // overlaps the id reservation above
     if (claim) {
       unsigned fresh = 0;
       if (n_claim > have) fresh = __shfl_sync(kFull, base, 0);
@@ -1021,7 +647,7 @@ struct PathC {
       } else {
         ids.next += n_claim;
       }
-      ids.inserted += n_claim;
+      ids.inserted += __popc(__ballot_sync(kFull, state == kClaimed && my_id < cv.max_entries));
       if (state == kClaimed) {
         unsigned long long* slot = cv.table + pos;
         if (my_id < cv.max_entries) {
@@ -1150,8 +776,8 @@ __global__ void __launch_bounds__(256, 4) k_unary_c(CacheView cv, uint32_t first
     built += __popc(en);
     __syncwarp();
   }
-  PathB<W, 1>::flush(pend);
-  PathB<W, 1>::retire(cv, idr);
+  WarpDedup::flush(pend);
+  WarpDedup::retire(cv, idr);
   if (lane == 0 && built) atomicAdd(&cv.ctr->built, built);
 }
 
@@ -1225,8 +851,8 @@ __global__ void __launch_bounds__(256, 4) k_binary_c(CacheView cv, BinaryPlan pl
     }
     __syncthreads();
   }
-  PathB<W, 1>::flush(pend);
-  PathB<W, 1>::retire(cv, idr);
+  WarpDedup::flush(pend);
+  WarpDedup::retire(cv, idr);
   if (lane == 0 && built) atomicAdd(&cv.ctr->built, built);
 }
 
@@ -1264,21 +890,21 @@ __global__ void __launch_bounds__(256, 4) k_desc_c(CacheView cv, const unsigned 
                              stage, pend, idr);
     __syncwarp();
   }
-  PathB<W, 1>::flush(pend);
-  PathB<W, 1>::retire(cv, idr);
+  WarpDedup::flush(pend);
+  WarpDedup::retire(cv, idr);
   if (implicit_atoms && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&cv.ctr->built, (unsigned long long)n);
 }
 
 // ===========================================================================
-// Path D (CMs above 4 KiB, e.g. 2048 traces of 64-bit words = 16 KiB): the
+// Path D (CMs above 512 bytes, e.g. 2048 traces of 64-bit words = 16 KiB): the
 // hash-first scheme of path C with rv = vecs / 32 vectors per lane, walked in
 // loops. Operand rows are read through L1/L2 whenever a candidate is
 // (re)computed; compares read the stored row directly.
 // ===========================================================================
 template <typename W>
 struct PathD {
-  using Pending = typename PathB<W, 1>::Pending;
-  using Ids = typename PathB<W, 1>::Ids;
+  using Pending = WarpDedup::Pending;
+  using Ids = WarpDedup::Ids;
 
   template <bool kEarlyPublish, class Gen>
   __device__ static void batch(const CacheView& cv, const Gen& gen, int n, uint32_t en, Pending& pend, Ids& ids) {
@@ -1305,9 +931,10 @@ struct PathD {
     const uint64_t my_desc = gen.desc(lane < n ? lane : 0);
     if (mine && !((bad >> lane) & 1u)) record_solution(cv, my_desc);
 
-    constexpr int kProbing = PathB<W, 1>::kProbing, kDone = PathB<W, 1>::kDone,
-                  kClaimed = PathB<W, 1>::kClaimed, kDeferred = PathB<W, 1>::kDeferred;
-    int state = mine ? kProbing : kDone;
+    constexpr int kProbing = WarpDedup::kProbing, kDone = WarpDedup::kDone,
+                  kClaimed = WarpDedup::kClaimed, kDeferred = WarpDedup::kDeferred;
+    const bool full = __any_sync(kFull, lane == 0 && ld_relaxed_u32(&cv.ctr->full) != 0u);
+    int state = (mine && !full) ? kProbing : kDone;  // a full arena: spec check only
     const uint64_t h = h_fin(my_hi, my_lo);
     const unsigned long long tag = (h >> 32) << 32;
     unsigned long long pos = h & cv.table_mask;
@@ -1324,7 +951,7 @@ struct PathD {
       const bool eq = !__any_sync(kFull, ne != 0u);
       if (lane == q && eq) state = kDone;
     }
-    if (kEarlyPublish) PathB<W, 1>::flush(pend);
+    if (kEarlyPublish) WarpDedup::flush(pend);
     uint32_t cmp_id = 0;
     unsigned long long guard = 0;
     while (true) {
@@ -1366,7 +993,7 @@ struct PathD {
     const unsigned have = ids.end - ids.next;
     unsigned base = 0;
     if (n_claim > have && lane == 0) base = atomicAdd(&cv.ctr->n_entries, max(cv.chunk, n_claim - have));
-    if (!kEarlyPublish) PathB<W, 1>::flush(pend);
+    if (!kEarlyPublish) WarpDedup::flush(pend);
     if (claim) {
       unsigned fresh = 0;
       if (n_claim > have) fresh = __shfl_sync(kFull, base, 0);
@@ -1387,7 +1014,7 @@ struct PathD {
       } else {
         ids.next += n_claim;
       }
-      ids.inserted += n_claim;
+      ids.inserted += __popc(__ballot_sync(kFull, state == kClaimed && my_id < cv.max_entries));
       if (state == kClaimed) {
         unsigned long long* slot = cv.table + pos;
         if (my_id < cv.max_entries) {
@@ -1481,8 +1108,8 @@ __global__ void __launch_bounds__(256) k_unary_d(CacheView cv, uint32_t first, u
     P::template batch<false>(cv, gen, int(4 * nrows), en, pend, idr);
     built += __popc(en);
   }
-  PathB<W, 1>::flush(pend);
-  PathB<W, 1>::retire(cv, idr);
+  WarpDedup::flush(pend);
+  WarpDedup::retire(cv, idr);
   if (lane == 0 && built) atomicAdd(&cv.ctr->built, built);
 }
 
@@ -1532,8 +1159,8 @@ __global__ void __launch_bounds__(256) k_binary_d(CacheView cv, BinaryPlan plan)
     }
     __syncwarp();
   }
-  PathB<W, 1>::flush(pend);
-  PathB<W, 1>::retire(cv, idr);
+  WarpDedup::flush(pend);
+  WarpDedup::retire(cv, idr);
   if (lane == 0 && built) atomicAdd(&cv.ctr->built, built);
 }
 
@@ -1562,8 +1189,8 @@ __global__ void __launch_bounds__(256) k_desc_d(CacheView cv, const unsigned lon
     P::template batch<false>(cv, gen, int(cnt), cnt >= 32u ? 0xFFFFFFFFu : ((1u << cnt) - 1u), pend, idr);
     __syncwarp();
   }
-  PathB<W, 1>::flush(pend);
-  PathB<W, 1>::retire(cv, idr);
+  WarpDedup::flush(pend);
+  WarpDedup::retire(cv, idr);
   if (implicit_atoms && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&cv.ctr->built, (unsigned long long)n);
 }
 
@@ -1650,42 +1277,6 @@ struct LaunchA {
   }
 };
 
-template <typename W, int RV>
-struct LaunchB {
-  static constexpr size_t kStageBytes = size_t(8) * PathB<W, RV>::kStage * sizeof(uint4);  // 8 warps
-  static void allow_smem(const void* fn) {
-    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-  }
-  static cudaError_t desc_list(const CacheView& cv, const unsigned long long* list, const unsigned int* list_n,
-                               unsigned int cap, unsigned int atoms, const LaunchCfg& lc) {
-    static bool once = (allow_smem((const void*)k_desc_b<W, RV>), true);
-    (void)once;
-    const unsigned n = list ? cap : atoms;
-    const unsigned per_block = 8u * PathB<W, RV>::NB;
-    const unsigned blocks = std::max(1u, std::min((n + per_block - 1) / per_block, unsigned(lc.sms * 3)));
-    k_desc_b<W, RV><<<blocks, 256, kStageBytes, lc.stream>>>(cv, list, list_n, cap, atoms);
-    return cudaGetLastError();
-  }
-  static cudaError_t unary(const CacheView& cv, uint32_t first, uint32_t count, uint32_t ops, const LaunchCfg& lc) {
-    static bool once = (allow_smem((const void*)k_unary_b<W, RV>), true);
-    (void)once;
-    static int occ = occupancy_blocks((const void*)k_unary_b<W, RV>, 256, kStageBytes);
-    const unsigned per_block = 8u * std::max(1, PathB<W, RV>::NB / 4);
-    const unsigned blocks = std::max(1u, std::min((count + per_block - 1) / per_block, unsigned(lc.sms * occ)));
-    k_unary_b<W, RV><<<blocks, 256, kStageBytes, lc.stream>>>(cv, first, count, ops);
-    return cudaGetLastError();
-  }
-  static cudaError_t binary(const CacheView& cv, const BinaryPlan& plan, const LaunchCfg& lc) {
-    static bool once = (allow_smem((const void*)k_binary_b<W, RV>), true);
-    (void)once;
-    const size_t smem = size_t(plan.tile) * cv.vecs * sizeof(uint4) + kStageBytes;
-    const int occ = occupancy_blocks((const void*)k_binary_b<W, RV>, 256, smem);
-    const unsigned long long blocks = std::max(1ull, std::min(plan.total_tiles, (unsigned long long)lc.sms * occ));
-    k_binary_b<W, RV><<<unsigned(blocks), 256, smem, lc.stream>>>(cv, plan);
-    return cudaGetLastError();
-  }
-};
-
 template <typename W>
 struct LaunchC {
   static constexpr size_t kUnarySmem = size_t(8) * (4 * 32 + PathC<W>::kStage) * sizeof(uint4);
@@ -1743,40 +1334,38 @@ struct LaunchD {
 template <typename W>
 int Kernels<W>::path_for(unsigned vecs) {
   if (vecs == 1 || vecs == 2 || vecs == 4 || vecs == 8) return 1;
-  if (vecs == 32 || vecs == 64 || vecs == 128 || vecs == 256) return 2;
+  if (vecs == 32) return 2;
+  if (vecs > 32 && vecs % 32 == 0 && vecs <= 4096) return 3;
   return 0;
 }
 
-#define LSYN_DISPATCH(vecs, CALL_A, CALL_B)             \
+#define LSYN_DISPATCH(vecs, CALL)                       \
   switch (vecs) {                                       \
-    case 1: return LaunchA<W, 1>::CALL_A;               \
-    case 2: return LaunchA<W, 2>::CALL_A;               \
-    case 4: return LaunchA<W, 4>::CALL_A;               \
-    case 8: return LaunchA<W, 8>::CALL_A;               \
-    case 32: return LaunchC<W>::CALL_B;                 \
-    case 64: return LaunchB<W, 2>::CALL_B;              \
-    case 128: return LaunchB<W, 4>::CALL_B;             \
-    case 256: return LaunchB<W, 8>::CALL_B;             \
+    case 1: return LaunchA<W, 1>::CALL;                 \
+    case 2: return LaunchA<W, 2>::CALL;                 \
+    case 4: return LaunchA<W, 4>::CALL;                 \
+    case 8: return LaunchA<W, 8>::CALL;                 \
+    case 32: return LaunchC<W>::CALL;                   \
     default:                                            \
-      if (vecs > 256 && vecs % 32 == 0) return LaunchD<W>::CALL_B; \
+      if (vecs > 32 && vecs % 32 == 0) return LaunchD<W>::CALL; \
       return cudaErrorInvalidValue;                     \
   }
 
 template <typename W>
 cudaError_t Kernels<W>::desc_list(const CacheView& cv, const unsigned long long* list, const unsigned int* list_n,
                                   unsigned int cap, unsigned int atoms, const LaunchCfg& lc) {
-  LSYN_DISPATCH(cv.vecs, desc_list(cv, list, list_n, cap, atoms, lc), desc_list(cv, list, list_n, cap, atoms, lc))
+  LSYN_DISPATCH(cv.vecs, desc_list(cv, list, list_n, cap, atoms, lc))
 }
 
 template <typename W>
 cudaError_t Kernels<W>::unary(const CacheView& cv, uint32_t first, uint32_t count, uint32_t ops,
                               const LaunchCfg& lc) {
-  LSYN_DISPATCH(cv.vecs, unary(cv, first, count, ops, lc), unary(cv, first, count, ops, lc))
+  LSYN_DISPATCH(cv.vecs, unary(cv, first, count, ops, lc))
 }
 
 template <typename W>
 cudaError_t Kernels<W>::binary(const CacheView& cv, const BinaryPlan& plan, const LaunchCfg& lc) {
-  LSYN_DISPATCH(cv.vecs, binary(cv, plan, lc), binary(cv, plan, lc))
+  LSYN_DISPATCH(cv.vecs, binary(cv, plan, lc))
 }
 
 template <typename W>

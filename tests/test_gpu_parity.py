@@ -236,6 +236,30 @@ def test_cache_full_path(L):
         assert ei.value.status == L.LSYN_E_STATE
 
 
+def test_cache_full_warp_path(L):
+    """512-byte matrices, 64 MiB cache: levels 1..6 stay exact, level 7 fills
+    the arena; deeper levels are refused and solve reports a full cache."""
+    p = W.mid_problem(2, oracle.labeller)
+    spec = oracle.Spec.from_problem(p)
+    run = spec.enumerate(6)
+    packed = L.pack_problem(p)
+    with L.Synthesizer(packed, L.make_config(cache_bytes=64 << 20, full_levels=True)) as s:
+        for k in range(1, 7):
+            st = s.level(k)
+            assert not st.cache_full
+            assert np.array_equal(canon(s.export(k)), canon(oracle_rows(run.cms(k), 32, p.n_traces)))
+        st = s.level(7)
+        assert st.cache_full == 1
+        rows = s.export(7)
+        assert canon(rows).shape[0] == rows.shape[0]
+        with pytest.raises(L.LsynError) as ei:
+            s.level(8)
+        assert ei.value.status == L.LSYN_E_STATE
+    with L.Synthesizer(packed, L.make_config(cache_bytes=64 << 20)) as s:
+        st, res, f, _ = s.solve(12)
+    assert st == L.LSYN_E_CACHE_FULL and res.found == 0
+
+
 def test_solve_reports_cache_full(L):
     g = GOLDEN["size16"]
     p = W.problem_from_strings("e3", g["positive"], g["negative"], g["props"])
