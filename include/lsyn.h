@@ -238,6 +238,60 @@ lsyn_status lsyn_eval(const lsyn_problem* problem, const char* formula, void* ds
                       const lsyn_config* config);
 
 /*
+ * Batched solving: many independent specifications enumerated together, one
+ * persistent launch per step over a packed work list of every unfinished
+ * problem, each at its own level (the listing of "A generic program
+ * synthesiser" applied to each problem; batching is this library's own).
+ *   problems   host array of n problem descriptions (same word_bits for all);
+ *              copied during the call.
+ *   config     shared by every problem; cache_bytes is PER PROBLEM. Device
+ *              memory of all problems stays allocated until lsyn_batch_destroy.
+ *   tuning     launch shape (NULL = defaults: 4 blocks per SM, no graph).
+ * Errors: as lsyn_create (the first failing problem is named in
+ * lsyn_batch_last_error(NULL)).
+ */
+typedef struct lsyn_batch lsyn_batch;
+typedef struct {
+  int32_t blocks_per_sm;  /* persistent blocks of 256 threads per SM (0 = 4) */
+  int32_t use_graph;      /* 1: replay the step (upload, reset, launch, copy back) from a CUDA graph */
+  int32_t reserved[2];
+} lsyn_batch_tuning;
+
+lsyn_status lsyn_batch_create(const lsyn_problem* problems, int32_t n, const lsyn_config* config,
+                              const lsyn_batch_tuning* tuning, lsyn_batch** out);
+
+/*
+ * Solve every problem up to max_size (1..17). results (host, n entries, each
+ * with its own caller-owned formula buffer) receive what lsyn_solve would
+ * return, ms = time from the start of this call to the problem's answer;
+ * statuses[i] receives the status lsyn_solve would return for problem i
+ * (LSYN_OK, LSYN_NOT_FOUND, LSYN_E_CACHE_FULL). The call itself returns
+ * LSYN_OK unless a CUDA error or a consistency check stops the whole batch.
+ */
+lsyn_status lsyn_batch_solve(lsyn_batch* batch, int32_t max_size, lsyn_result* results, int32_t* statuses);
+
+/*
+ * Autotuner: solves the batch (up to max_size) once per candidate launch shape
+ * (blocks per SM in {2, 4, 6, 8}, with and without the step graph), keeps the
+ * fastest for later lsyn_batch_solve calls and writes it to *out (may be NULL).
+ */
+lsyn_status lsyn_batch_autotune(lsyn_batch* batch, int32_t max_size, lsyn_batch_tuning* out);
+
+/*
+ * Problem i of the batch as a context handle owned by the batch (valid until
+ * lsyn_batch_destroy; do not pass it to lsyn_destroy). Read-only calls
+ * (lsyn_level_count, lsyn_export_level, lsyn_entry_formula) inspect the levels
+ * the batch built for that problem.
+ */
+lsyn_status lsyn_batch_problem(lsyn_batch* batch, int32_t i, lsyn_ctx** out);
+
+/* Message of the last error of the batch (NULL: of the last failed lsyn_batch_create on this thread). */
+const char* lsyn_batch_last_error(const lsyn_batch* batch);
+
+/* Release the batch and every problem's device memory. NULL is allowed. */
+void lsyn_batch_destroy(lsyn_batch* batch);
+
+/*
  * Formula evaluation that allocates no device memory (the paper has no
  * counterpart; it is a service for callers that cannot call cudaMalloc, such
  * as a process whose memory manager owns every device allocation, or a

@@ -206,5 +206,5 @@ def labeller(formula: str, traces, n_props: int) -> np.ndarray:
     bits = np.asarray(traces.bits, dtype=np.int64)
     masks = (bits << np.arange(n_props, dtype=np.int64)[None, None, :]).sum(axis=2)
     s = Spec(n_props, traces.lengths, masks.astype(np.int32), len(traces.lengths))
-    cm = s.eval(formula)
+    cm = s.eval_seq(formula)  # bottom-up, O(length^2) per node; pinned equal to the recursive definition
     return np.array([seq[:1] == "1" for seq in cm.split(",")], dtype=bool)

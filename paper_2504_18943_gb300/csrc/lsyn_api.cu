@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "lsyn.h"
+#include "lsyn_ctx.h"
 #include "lsyn_internal.h"
 
 using namespace lsyn;
@@ -26,153 +27,19 @@ namespace {
 
 thread_local std::string g_create_error;
 
-struct Alloc {
-  lsyn_alloc_fn alloc = nullptr;
-  lsyn_free_fn free = nullptr;
-  void* user = nullptr;
-  std::vector<void*> owned;
-  void* get(size_t bytes) {
-    if (bytes == 0) bytes = 16;
-    void* p = nullptr;
-    if (alloc) {
-      p = alloc(bytes, user);
-    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
-      cudaGetLastError();
-      p = nullptr;
-    }
-    if (p) owned.push_back(p);
-    return p;
-  }
-  void release_all() {
-    for (void* p : owned) {
-      if (free) free(p, user);
-      else cudaFree(p);
-    }
-    owned.clear();
-  }
-};
-
-// Bit reversal within a word: the ABI numbers positions from the least
-// significant bit (bit t = position t); inside the library position 0 is the
-// most significant bit, as the paper writes characteristic sequences.
-uint32_t rev32(uint32_t x) {
-  x = ((x >> 1) & 0x55555555u) | ((x & 0x55555555u) << 1);
-  x = ((x >> 2) & 0x33333333u) | ((x & 0x33333333u) << 2);
-  x = ((x >> 4) & 0x0F0F0F0Fu) | ((x & 0x0F0F0F0Fu) << 4);
-  x = ((x >> 8) & 0x00FF00FFu) | ((x & 0x00FF00FFu) << 8);
-  return (x >> 16) | (x << 16);
-}
-
-uint64_t rev64(uint64_t x) { return (uint64_t(rev32(uint32_t(x))) << 32) | rev32(uint32_t(x >> 32)); }
-
-void reverse_words(void* data, size_t n_words, int word_bits) {
-  if (word_bits == 32) {
-    uint32_t* w = static_cast<uint32_t*>(data);
-    for (size_t i = 0; i < n_words; ++i) w[i] = rev32(w[i]);
-  } else {
-    uint64_t* w = static_cast<uint64_t*>(data);
-    for (size_t i = 0; i < n_words; ++i) w[i] = rev64(w[i]);
-  }
-}
-
 uint32_t mix32(uint32_t x) {
   x ^= x >> 16; x *= 0x7FEB352Du; x ^= x >> 15; x *= 0x846CA68Bu; x ^= x >> 16;
   return x;
 }
 
-double now_ms() {
-  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
-}
-
-struct Snap {
-  DevCounters c;
-};
 
 }  // namespace
 
 std::string& lsyn::thread_error() { return g_create_error; }
 
-struct lsyn_ctx {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  Alloc mem;
-  uint32_t op_mask = LSYN_OPS_ALL;
-  bool full_levels = false;
-  bool timing = false;
-  // problem
-  int n_props = 0, n_pos = 0, n_neg = 0, T = 0, word_bits = 32, max_len = 1, steps = 0;
-  unsigned vecs = 0;
-  int path = 0;
-  int sms = 1;
-  // device memory
-  uint4* arena = nullptr;
-  unsigned long long* prov = nullptr;
-  unsigned long long* table = nullptr;
-  unsigned long long table_cap = 0;
-  unsigned max_entries = 0;
-  DevCounters* ctr = nullptr;
-  uint4* consts = nullptr;  // [5][vecs]: lenmask, label, care, key, mul
-  uint4* atoms = nullptr;   // [n_props][vecs]
-  unsigned long long* defer[2] = {nullptr, nullptr};
-  unsigned defer_cap = 0;
-  unsigned* slotpos = nullptr;  // [max_entries]
-  uint2* holes = nullptr;       // [hole_cap]
-  unsigned hole_cap = 0;
-  uint2* moves = nullptr;       // [move_cap]
-  unsigned move_cap = 0;
-  unsigned chunk = 1;
-  char* fbuf = nullptr;
-  int* fstatus = nullptr;
-  static constexpr unsigned kFormulaCap = 1u << 16;
-  // host mirrors
-  Snap* h_snap = nullptr;  // pinned, kSnaps entries
-  static constexpr int kSnaps = 80;
-  char* h_fbuf = nullptr;  // pinned formula text
-  int* h_fstatus = nullptr;
-  std::vector<uint32_t> level_start, level_n;  // indexed by level
-  int levels_done = 0;
-  bool last_incomplete = false;
-  unsigned long long constructed = 0;
-  unsigned long long last_sol = ~0ull;
-  cudaEvent_t ev[2 * 80] = {};
-  bool events_ready = false;
-  std::string err;
-
-  lsyn_status fail(lsyn_status s, const std::string& msg) {
-    err = msg;
-    return s;
-  }
-  lsyn_status cuda_fail(cudaError_t e, const char* where) {
-    err = std::string(where) + ": " + cudaGetErrorString(e);
-    return LSYN_E_CUDA;
-  }
-  CacheView view(unsigned long long* defer_out, unsigned* defer_out_n) const {
-    CacheView cv;
-    cv.arena = arena;
-    cv.prov = prov;
-    cv.table = table;
-    cv.table_mask = table_cap - 1;
-    cv.max_entries = max_entries;
-    cv.vecs = vecs;
-    cv.ctr = ctr;
-    cv.lenmask = consts;
-    cv.label = consts + vecs;
-    cv.care = consts + 2 * vecs;
-    cv.hkey = consts + 3 * vecs;
-    cv.hmul = consts + 4 * vecs;
-    cv.atoms = atoms;
-    cv.defer_out = defer_out;
-    cv.defer_out_n = defer_out_n;
-    cv.defer_cap = defer_cap;
-    cv.slotpos = slotpos;
-    cv.holes = holes;
-    cv.hole_cap = hole_cap;
-    cv.chunk = chunk;
-    cv.steps = steps;
-    cv.early_exit = full_levels ? 0 : 1;
-    return cv;
-  }
-};
+double lsyn::now_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
 
 namespace {
 
@@ -262,7 +129,9 @@ lsyn_status launch_desc(lsyn_ctx* c, const CacheView& cv, const unsigned long lo
   return e == cudaSuccess ? LSYN_OK : c->cuda_fail(e, "desc kernel");
 }
 
-lsyn_status reconstruct(lsyn_ctx* c, const unsigned long long* root_ptr, char* out, size_t cap) {
+}  // namespace
+
+lsyn_status lsyn::ctx_reconstruct(lsyn_ctx* c, const unsigned long long* root_ptr, char* out, size_t cap) {
   k_reconstruct<<<1, 1, 0, c->stream>>>(c->prov, 0, root_ptr, c->fbuf, lsyn_ctx::kFormulaCap, c->fstatus);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return c->cuda_fail(e, "reconstruct");
@@ -276,6 +145,8 @@ lsyn_status reconstruct(lsyn_ctx* c, const unsigned long long* root_ptr, char* o
   memcpy(out, c->h_fbuf, len + 1);
   return LSYN_OK;
 }
+
+namespace {
 
 // Parse prefix formula text into a postorder node list (children first).
 bool parse_formula(const char* s, int n_props, std::vector<int4>* nodes, std::string* err) {
@@ -412,6 +283,125 @@ void pack_host(const lsyn_problem* p, const Layout& L, unsigned vecs, std::vecto
 
 }  // namespace
 
+
+uint32_t lsyn::plan_hole_moves(const uint2* holes, unsigned n, uint32_t start, uint32_t total,
+                               std::vector<uint2>* mv) {
+  std::vector<std::pair<uint32_t, uint32_t>> rng;
+  for (unsigned i = 0; i < n; ++i) {
+    const uint32_t lo = std::max(holes[i].x, start), hi = std::min(holes[i].y, total);
+    if (lo < hi) rng.push_back({lo, hi});
+  }
+  std::sort(rng.begin(), rng.end());
+  uint64_t H = 0;
+  for (auto& r : rng) H += r.second - r.first;
+  const uint32_t dense_end = total - uint32_t(H);
+  size_t ri = 0;  // range holding or following the next valid candidate id >= dense_end
+  uint32_t v = dense_end;
+  auto next_valid = [&]() {
+    while (ri < rng.size() && rng[ri].second <= v) ++ri;
+    while (ri < rng.size() && rng[ri].first <= v && v < rng[ri].second) { v = rng[ri].second; ++ri; }
+  };
+  for (auto& r : rng) {
+    for (uint32_t hole = r.first; hole < r.second && hole < dense_end; ++hole) {
+      next_valid();
+      mv->push_back(make_uint2(v, hole));
+      ++v;
+    }
+  }
+  return dense_end;
+}
+
+void lsyn::ctx_level_plan(lsyn_ctx* c, int k, LevelPlan* lp) {
+  *lp = LevelPlan();
+  memset(&lp->plan, 0, sizeof(lp->plan));
+  lp->start = c->level_start.back() + c->level_n.back();
+  // Ids a warp reserves at a time: large enough to keep the shared counter
+  // cold, small enough that the reservations of every resident warp stay a
+  // small part of the free arena.
+  {
+    const unsigned long long free_ids = c->max_entries > lp->start ? c->max_entries - lp->start : 0;
+    const unsigned long long warps = (unsigned long long)c->sms * 24ull;
+    c->chunk = unsigned(std::max(1ull, std::min(32ull, free_ids / (8ull * warps))));
+  }
+  const double M = double(c->vecs) * 16.0;
+  if (k == 1) {
+    lp->op_bytes_unary = double(c->n_props) * M;
+    return;
+  }
+  const uint32_t m = c->op_mask;
+  lp->uops = ((m & LSYN_OP_NOT) ? 1u : 0u) | ((m & LSYN_OP_X) ? 2u : 0u) | ((m & LSYN_OP_F) ? 4u : 0u) |
+             ((m & LSYN_OP_G) ? 8u : 0u);
+  lp->u_first = c->level_start[k - 1];
+  lp->u_count = lp->uops ? c->level_n[k - 1] : 0;
+  lp->op_bytes_unary = double(lp->u_count) * M;
+  const uint32_t bops = ((m & LSYN_OP_AND) ? 1u : 0u) | ((m & LSYN_OP_OR) ? 2u : 0u) | ((m & LSYN_OP_U) ? 12u : 0u);
+  if (!bops || k < 3) return;
+  BinaryPlan& plan = lp->plan;
+  plan.ops = bops;
+  plan.work_slot = 0;
+  plan.tile = c->path == 2 ? std::max(1u, std::min(32u, unsigned((48 * 1024) / (c->vecs * 16)))) : 1u;
+  unsigned long long tiles = 0, pairs = 0;
+  for (int i = 1; 2 * i <= k - 1; ++i) {
+    const int j = k - 1 - i;
+    const uint32_t ni = c->level_n[i], nj = c->level_n[j];
+    if (!ni || !nj || (i == j && ni < 2)) continue;
+    Split sp;
+    memset(&sp, 0, sizeof(sp));
+    if (i == j || ni <= nj) {
+      sp.left_start = c->level_start[i]; sp.left_n = ni;
+      sp.right_start = c->level_start[j]; sp.right_n = nj;
+    } else {
+      sp.left_start = c->level_start[j]; sp.left_n = nj;
+      sp.right_start = c->level_start[i]; sp.right_n = ni;
+    }
+    sp.tri = i == j ? 1u : 0u;
+    sp.lt_tiles = (sp.left_n + plan.tile - 1) / plan.tile;
+    sp.rt_tiles = (sp.right_n + plan.tile - 1) / plan.tile;
+    sp.tiles_begin = tiles;
+    sp.pairs_begin = pairs;
+    sp.pairs = (unsigned long long)sp.left_n * sp.right_n;
+    tiles += (unsigned long long)sp.lt_tiles * sp.rt_tiles;
+    pairs += sp.pairs;
+    lp->op_bytes_binary += double(sp.left_n + (sp.tri ? 0u : sp.right_n)) * M;
+    plan.s[plan.n_splits++] = sp;
+  }
+  plan.total_tiles = tiles;
+  plan.total_pairs = pairs;
+}
+
+lsyn_status lsyn::ctx_commit_level(lsyn_ctx* c, int k, const DevCounters& h, uint32_t total,
+                                   unsigned long long deferred, const LevelPlan& lp, lsyn_level_stats* out) {
+  const uint32_t start = lp.start;
+  const uint32_t unique = total - start;
+  if (h.inserted != unique)
+    return c->fail(LSYN_E_STATE, "insert count " + std::to_string(h.inserted) + " differs from the level size " +
+                                     std::to_string(unique));
+  c->level_start.push_back(start);
+  c->level_n.push_back(unique);
+  c->levels_done = k;
+  std::vector<int64_t> sizes(c->level_n.begin() + 1, c->level_n.end());
+  const int64_t planned = k == 1 ? c->n_props : level_candidates(sizes.data(), k, c->op_mask);
+  const bool stopped = h.solved && c->full_levels == false && int64_t(h.built) < planned;
+  c->last_incomplete = h.full || stopped;
+  c->constructed += h.built;
+  c->last_sol = h.solved ? h.sol : ~0ull;
+  if (out) {
+    memset(out, 0, sizeof(*out));
+    out->level = k;
+    out->solved = h.solved ? 1 : 0;
+    out->cache_full = h.full ? 1 : 0;
+    out->early_exit = stopped ? 1 : 0;
+    out->candidates = int64_t(h.built);
+    out->unique = unique;
+    out->total = total;
+    out->deferred = int64_t(deferred);
+    const double M = double(c->vecs) * 16.0;
+    const double C = double(h.built), U = double(unique);
+    out->bytes_alg = lp.op_bytes_unary + lp.op_bytes_binary + C * 32.0 + (C - U) * M + U * (M + 16.0);
+  }
+  return LSYN_OK;
+}
+
 extern "C" {
 
 const char* lsyn_version(void) { return "lsyn 0.1 (sm_103a)"; }
@@ -443,6 +433,13 @@ void lsyn_destroy(lsyn_ctx* c) {
 }
 
 lsyn_status lsyn_create(const lsyn_problem* problem, const lsyn_config* config, lsyn_ctx** out) {
+  return lsyn::ctx_create(problem, config, false, out);
+}
+
+}  // extern "C"
+
+lsyn_status lsyn::ctx_create(const lsyn_problem* problem, const lsyn_config* config, bool warp_layout,
+                             lsyn_ctx** out) {
   g_create_error.clear();
   if (!out) { g_create_error = "out is NULL"; return LSYN_E_INVAL; }
   *out = nullptr;
@@ -463,7 +460,7 @@ lsyn_status lsyn_create(const lsyn_problem* problem, const lsyn_config* config, 
   // of 16-byte vectors; C (one vector per lane) up to 512 bytes; D (whole
   // warps of vectors, looped per lane) up to 64 KiB.
   unsigned vecs = 0;
-  if (L.vecs_needed <= 8) {
+  if (L.vecs_needed <= 8 && !warp_layout) {
     vecs = 1;
     while (vecs < L.vecs_needed) vecs <<= 1;
   } else if (L.vecs_needed <= 4096) {
@@ -503,7 +500,7 @@ lsyn_status lsyn_create(const lsyn_problem* problem, const lsyn_config* config, 
   c->max_len = L.max_len;
   c->steps = L.steps;
   c->vecs = vecs;
-  c->path = L.vecs_needed <= 8 ? 1 : vecs == 32 ? 2 : 3;
+  c->path = vecs <= 8 ? 1 : vecs == 32 ? 2 : 3;
   c->table_cap = best_cap;
   c->max_entries = unsigned(best_e);
   c->defer_cap = unsigned(std::max(1ull << 16, std::min(1ull << 23, best_e / 16)));
@@ -563,6 +560,8 @@ lsyn_status lsyn_create(const lsyn_problem* problem, const lsyn_config* config, 
   return LSYN_OK;
 }
 
+extern "C" {
+
 lsyn_status lsyn_reset(lsyn_ctx* c) {
   if (!c) return LSYN_E_INVAL;
   cudaSetDevice(c->device);
@@ -599,15 +598,9 @@ lsyn_status lsyn_enumerate_level(lsyn_ctx* c, int32_t k, lsyn_level_stats* out) 
     ++evn;
   };
 
-  const uint32_t start = c->level_start.back() + c->level_n.back();
-  // Ids a warp reserves at a time: large enough to keep the shared counter
-  // cold, small enough that the reservations of every resident warp stay a
-  // small part of the free arena.
-  {
-    const unsigned long long free_ids = c->max_entries > start ? c->max_entries - start : 0;
-    const unsigned long long warps = (unsigned long long)c->sms * 24ull;
-    c->chunk = unsigned(std::max(1ull, std::min(32ull, free_ids / (8ull * warps))));
-  }
+  LevelPlan lp;
+  ctx_level_plan(c, k, &lp);
+  const uint32_t start = lp.start;
   int launches = 0;
   ev_begin();
   k_level_begin<<<1, 1, 0, c->stream>>>(c->ctr);
@@ -618,7 +611,6 @@ lsyn_status lsyn_enumerate_level(lsyn_ctx* c, int32_t k, lsyn_level_stats* out) 
 
   CacheView cv = c->view(c->defer[0], &c->ctr->defer_n[0]);
   int binary_snap = -1, unary_snap = -1;
-  double op_bytes_unary = 0, op_bytes_binary = 0;
   const double M = double(c->vecs) * 16.0;
   if (k == 1) {
     ev_begin();
@@ -627,66 +619,25 @@ lsyn_status lsyn_enumerate_level(lsyn_ctx* c, int32_t k, lsyn_level_stats* out) 
     if (s != LSYN_OK) return s;
     ev_end(3);
     if ((e = take_snap()) != cudaSuccess) return c->cuda_fail(e, "snapshot");
-    op_bytes_unary = double(c->n_props) * M;
   } else {
-    const uint32_t m = c->op_mask;
-    const uint32_t uops = ((m & LSYN_OP_NOT) ? 1u : 0u) | ((m & LSYN_OP_X) ? 2u : 0u) |
-                          ((m & LSYN_OP_F) ? 4u : 0u) | ((m & LSYN_OP_G) ? 8u : 0u);
-    const uint32_t prev_n = c->level_n[k - 1];
-    if (uops && prev_n) {
+    if (lp.uops && lp.u_count) {
       ev_begin();
-      e = c->word_bits == 32 ? Kernels<uint32_t>::unary(cv, c->level_start[k - 1], prev_n, uops, lc)
-                             : Kernels<uint64_t>::unary(cv, c->level_start[k - 1], prev_n, uops, lc);
+      e = c->word_bits == 32 ? Kernels<uint32_t>::unary(cv, lp.u_first, lp.u_count, lp.uops, lc)
+                             : Kernels<uint64_t>::unary(cv, lp.u_first, lp.u_count, lp.uops, lc);
       ++launches;
       if (e != cudaSuccess) return c->cuda_fail(e, "unary kernel");
       ev_end(0);
       if ((e = take_snap()) != cudaSuccess) return c->cuda_fail(e, "snapshot");
       unary_snap = snap - 1;
-      op_bytes_unary = double(prev_n) * M;
     }
-    const uint32_t bops = ((m & LSYN_OP_AND) ? 1u : 0u) | ((m & LSYN_OP_OR) ? 2u : 0u) | ((m & LSYN_OP_U) ? 12u : 0u);
-    if (bops && k >= 3) {
-      BinaryPlan plan;
-      memset(&plan, 0, sizeof(plan));
-      plan.ops = bops;
-      plan.work_slot = 0;
-      plan.tile = c->path == 2 ? std::max(1u, std::min(32u, unsigned((48 * 1024) / (c->vecs * 16)))) : 1u;
-      unsigned long long tiles = 0, pairs = 0;
-      for (int i = 1; 2 * i <= k - 1; ++i) {
-        const int j = k - 1 - i;
-        const uint32_t ni = c->level_n[i], nj = c->level_n[j];
-        if (!ni || !nj || (i == j && ni < 2)) continue;
-        Split sp;
-        memset(&sp, 0, sizeof(sp));
-        if (i == j || ni <= nj) {
-          sp.left_start = c->level_start[i]; sp.left_n = ni;
-          sp.right_start = c->level_start[j]; sp.right_n = nj;
-        } else {
-          sp.left_start = c->level_start[j]; sp.left_n = nj;
-          sp.right_start = c->level_start[i]; sp.right_n = ni;
-        }
-        sp.tri = i == j ? 1u : 0u;
-        sp.lt_tiles = (sp.left_n + plan.tile - 1) / plan.tile;
-        sp.rt_tiles = (sp.right_n + plan.tile - 1) / plan.tile;
-        sp.tiles_begin = tiles;
-        sp.pairs_begin = pairs;
-        sp.pairs = (unsigned long long)sp.left_n * sp.right_n;
-        tiles += (unsigned long long)sp.lt_tiles * sp.rt_tiles;
-        pairs += sp.pairs;
-        op_bytes_binary += double(sp.left_n + (sp.tri ? 0u : sp.right_n)) * M;
-        plan.s[plan.n_splits++] = sp;
-      }
-      plan.total_tiles = tiles;
-      plan.total_pairs = pairs;
-      if (plan.n_splits > 0) {
-        ev_begin();
-        e = c->word_bits == 32 ? Kernels<uint32_t>::binary(cv, plan, lc) : Kernels<uint64_t>::binary(cv, plan, lc);
-        ++launches;
-        if (e != cudaSuccess) return c->cuda_fail(e, "binary kernel");
-        ev_end(1);
-        if ((e = take_snap()) != cudaSuccess) return c->cuda_fail(e, "snapshot");
-        binary_snap = snap - 1;
-      }
+    if (lp.plan.n_splits > 0) {
+      ev_begin();
+      e = c->word_bits == 32 ? Kernels<uint32_t>::binary(cv, lp.plan, lc) : Kernels<uint64_t>::binary(cv, lp.plan, lc);
+      ++launches;
+      if (e != cudaSuccess) return c->cuda_fail(e, "binary kernel");
+      ev_end(1);
+      if ((e = take_snap()) != cudaSuccess) return c->cuda_fail(e, "snapshot");
+      binary_snap = snap - 1;
     }
   }
   if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return c->cuda_fail(e, "level sync");
@@ -726,29 +677,8 @@ lsyn_status lsyn_enumerate_level(lsyn_ctx* c, int32_t k, lsyn_level_stats* out) 
     e = cudaMemcpyAsync(hr.data(), c->holes, hr.size() * sizeof(uint2), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return c->cuda_fail(e, "hole log copy");
-    std::vector<std::pair<uint32_t, uint32_t>> rng;
-    for (const uint2& r : hr) {
-      const uint32_t lo = std::max(r.x, start), hi = std::min(r.y, total);
-      if (lo < hi) rng.push_back({lo, hi});
-    }
-    std::sort(rng.begin(), rng.end());
-    uint64_t H = 0;
-    for (auto& r : rng) H += r.second - r.first;
-    const uint32_t dense_end = total - uint32_t(H);
     std::vector<uint2> mv;
-    size_t ri = 0;  // range holding or following the next valid candidate id >= dense_end
-    uint32_t v = dense_end;
-    auto next_valid = [&]() {
-      while (ri < rng.size() && rng[ri].second <= v) ++ri;
-      while (ri < rng.size() && rng[ri].first <= v && v < rng[ri].second) { v = rng[ri].second; ++ri; }
-    };
-    for (auto& r : rng) {
-      for (uint32_t hole = r.first; hole < r.second && hole < dense_end; ++hole) {
-        next_valid();
-        mv.push_back(make_uint2(v, hole));
-        ++v;
-      }
-    }
+    const uint32_t dense_end = plan_hole_moves(hr.data(), unsigned(hr.size()), start, total, &mv);
     if (mv.size() > c->move_cap) return c->fail(LSYN_E_STATE, "too many hole moves");
     if (!mv.empty()) {
       e = cudaMemcpyAsync(c->moves, mv.data(), mv.size() * sizeof(uint2), cudaMemcpyHostToDevice, c->stream);
@@ -768,33 +698,10 @@ lsyn_status lsyn_enumerate_level(lsyn_ctx* c, int32_t k, lsyn_level_stats* out) 
     if (c->h_snap[snap - 1].c.error) return c->fail(LSYN_E_STATE, "hole fixup found an inconsistent slot");
     total = dense_end;
   }
-  const uint32_t unique = total - start;
-  if (c->h_snap[snap - 1].c.inserted != unique)
-    return c->fail(LSYN_E_STATE, "insert count " + std::to_string(c->h_snap[snap - 1].c.inserted) +
-                                     " differs from the level size " + std::to_string(unique));
-  c->level_start.push_back(start);
-  c->level_n.push_back(unique);
-  c->levels_done = k;
-  std::vector<int64_t> sizes(c->level_n.begin() + 1, c->level_n.end());
-  const int64_t planned = k == 1 ? c->n_props : level_candidates(sizes.data(), k, c->op_mask);
-  const bool stopped = h.solved && c->full_levels == false && int64_t(h.built) < planned;
-  c->last_incomplete = h.full || stopped;
-  c->constructed += h.built;
-  c->last_sol = h.solved ? h.sol : ~0ull;
-
+  lsyn_status st = ctx_commit_level(c, k, c->h_snap[snap - 1].c, total, deferred, lp, out);
+  if (st != LSYN_OK) return st;
   if (out) {
-    memset(out, 0, sizeof(*out));
-    out->level = k;
-    out->solved = h.solved ? 1 : 0;
-    out->cache_full = h.full ? 1 : 0;
-    out->early_exit = stopped ? 1 : 0;
-    out->candidates = int64_t(h.built);
-    out->unique = unique;
-    out->total = total;
-    out->deferred = int64_t(deferred);
     out->launches = launches;
-    const double C = double(h.built), U = double(unique);
-    out->bytes_alg = op_bytes_unary + op_bytes_binary + C * 32.0 + (C - U) * M + U * (M + 16.0);
     // Per launch, from its exact built / inserted counters: operands, one table
     // sector per candidate, a compare read per duplicate, CM + provenance +
     // slot per insert.
@@ -805,8 +712,8 @@ lsyn_status lsyn_enumerate_level(lsyn_ctx* c, int32_t k, lsyn_level_stats* out) 
       const double Ul = double(b1.inserted - b0.inserted);
       return operands + Cl * 32.0 + (Cl - Ul) * M + Ul * (M + 16.0);
     };
-    if (binary_snap >= 0) out->bytes_binary = launch_bytes(binary_snap, op_bytes_binary);
-    if (unary_snap >= 0) out->bytes_unary = launch_bytes(unary_snap, op_bytes_unary);
+    if (binary_snap >= 0) out->bytes_binary = launch_bytes(binary_snap, lp.op_bytes_binary);
+    if (unary_snap >= 0) out->bytes_unary = launch_bytes(unary_snap, lp.op_bytes_unary);
     if (c->timing) {
       for (int i = 0; i < evn; ++i) {
         float ms = 0;
@@ -835,7 +742,7 @@ lsyn_status lsyn_solve(lsyn_ctx* c, int32_t max_size, lsyn_result* out) {
     if (out->level_stats && k <= out->level_stats_cap) out->level_stats[k - 1] = st;
     if (st.solved) {
       out->launches += 1;
-      s = reconstruct(c, &c->ctr->sol, out->formula, out->formula_cap);
+      s = ctx_reconstruct(c, &c->ctr->sol, out->formula, out->formula_cap);
       if (s != LSYN_OK) { result = s; break; }
       out->found = 1;
       out->size = k;
@@ -881,7 +788,7 @@ lsyn_status lsyn_export_level(lsyn_ctx* c, int32_t k, int64_t first, int64_t cou
 lsyn_status lsyn_entry_formula(lsyn_ctx* c, int32_t k, int64_t index, char* buf, size_t cap) {
   if (!c || k < 1 || k > c->levels_done || index < 0 || uint64_t(index) >= c->level_n[k]) return LSYN_E_INVAL;
   cudaSetDevice(c->device);
-  return reconstruct(c, c->prov + c->level_start[k] + size_t(index), buf, cap);
+  return ctx_reconstruct(c, c->prov + c->level_start[k] + size_t(index), buf, cap);
 }
 
 lsyn_status lsyn_eval(const lsyn_problem* problem, const char* formula, void* dst, const lsyn_config* config) {

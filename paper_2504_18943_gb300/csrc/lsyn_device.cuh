@@ -1195,6 +1195,196 @@ __global__ void __launch_bounds__(256) k_desc_d(CacheView cv, const unsigned lon
 }
 
 // ===========================================================================
+// Batch kernels: the path-D engine over many problems at once. Work items of
+// every problem in the step form one index space (per-problem prefix sums in
+// StepProblem); warps pull items from a counter, so uneven problems share the
+// GPU. When a warp moves to another problem it publishes its pending slots,
+// returns its unused ids to that problem's hole log and adds its built count.
+// ===========================================================================
+__device__ __forceinline__ int find_problem(const StepProblem* steps, int n, unsigned long long item, int which) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {  // last problem whose begin <= item
+    const int mid = (lo + hi + 1) >> 1;
+    const unsigned long long b = which == 0 ? steps[mid].d_items_begin
+                               : which == 1 ? steps[mid].u_items_begin : steps[mid].b_items_begin;
+    if (b <= item) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename W>
+struct BatchWarp {
+  int cur = -1;
+  unsigned long long built = 0;
+  WarpDedup::Pending pend;
+  WarpDedup::Ids ids;
+
+  // Make problem p current; its CacheView is copied to this warp's shared slot.
+  __device__ void enter(const StepProblem* steps, int p, CacheView* s_cv) {
+    if (p == cur) return;
+    leave(s_cv);
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(&steps[p].cv);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(s_cv);
+    for (int i = threadIdx.x & 31; i < int(sizeof(CacheView) / 4); i += 32) dst[i] = src[i];
+    __syncwarp();
+    cur = p;
+  }
+  __device__ void leave(CacheView* s_cv) {
+    if (cur < 0) return;
+    WarpDedup::flush(pend);
+    WarpDedup::retire(*s_cv, ids);
+    if ((threadIdx.x & 31) == 0 && built) atomicAdd(&s_cv->ctr->built, built);
+    built = 0;
+    __syncwarp();
+    cur = -1;
+  }
+};
+
+__device__ __forceinline__ unsigned long long grab(unsigned long long* counter) {
+  unsigned long long it = 0;
+  if ((threadIdx.x & 31) == 0) it = atomicAdd(counter, 1ull);
+  return __shfl_sync(kFull, it, 0);
+}
+
+template <typename W>
+__global__ void __launch_bounds__(256) k_batch_run(StepHeader* hdr, const StepProblem* steps) {
+  __shared__ CacheView s_cv[8];
+  __shared__ uint2 s_pairs[8][8];
+  __shared__ uint64_t s_d[8][32];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  CacheView* cv = &s_cv[wib];
+  const int n = hdr->n;
+  BatchWarp<W> bw;
+  // 1. descriptors: atoms of problems at level 1, deferred re-examination
+  for (unsigned long long it = grab(&hdr->work[0]); it < hdr->total_d; it = grab(&hdr->work[0])) {
+    const int p = find_problem(steps, n, it, 0);
+    bw.enter(steps, p, cv);
+    const StepProblem& sp = steps[p];
+    const uint32_t base = uint32_t(it - sp.d_items_begin) * 32u;
+    const uint32_t cnt = min(32u, sp.d_n - base);
+    s_d[wib][lane] = lane < int(cnt) ? (sp.d_list ? sp.d_list[base + lane] : pack_desc(kAtom, base + lane, 0))
+                                     : pack_desc(kAtom, 0, 0);
+    __syncwarp();
+    ListGenD<W> gen;
+    gen.cv = cv;
+    gen.d = s_d[wib];
+    PathD<W>::template batch<false>(*cv, gen, int(cnt), cnt >= 32u ? 0xFFFFFFFFu : ((1u << cnt) - 1u), bw.pend,
+                                    bw.ids);
+    if (!sp.d_list) bw.built += cnt;  // atoms count as built; deferred ones were counted when first built
+    __syncwarp();
+  }
+  // 2. unary operators, 8 rows (32 candidates) per item
+  for (unsigned long long it = grab(&hdr->work[1]); it < hdr->total_u; it = grab(&hdr->work[1])) {
+    const int p = find_problem(steps, n, it, 1);
+    bw.enter(steps, p, cv);
+    if (__any_sync(kFull, stop_requested(*cv))) continue;
+    const StepProblem& sp = steps[p];
+    const uint32_t base = uint32_t(it - sp.u_items_begin) * 8u;
+    const uint32_t nrows = min(8u, sp.u_count - base);
+    RowGenD<W> gen;
+    gen.cv = cv;
+    gen.id0 = sp.u_first + base;
+    uint32_t en = 0;
+#pragma unroll
+    for (int q = 0; q < 32; ++q) en |= ((sp.u_ops >> (q & 3)) & 1u & (uint32_t(q >> 2) < nrows ? 1u : 0u)) << q;
+    PathD<W>::template batch<false>(*cv, gen, int(4 * nrows), en, bw.pend, bw.ids);
+    bw.built += __popc(en);
+  }
+  // 3. binary operators, 8 pairs (32 candidates) per item
+  for (unsigned long long it = grab(&hdr->work[2]); it < hdr->total_b; it = grab(&hdr->work[2])) {
+    const int p = find_problem(steps, n, it, 2);
+    bw.enter(steps, p, cv);
+    if (__any_sync(kFull, stop_requested(*cv))) continue;
+    const StepProblem& sp = steps[p];
+    const unsigned long long g0 = (it - sp.b_items_begin) * 8ull;
+    uint32_t ok = 0;
+    if (lane < 8) {
+      unsigned long long pidx = g0 + lane;
+      int si = 0;
+      while (si + 1 < int(sp.n_splits) && sp.s[si + 1].pairs_begin <= pidx) ++si;
+      const Split& S = sp.s[si];
+      const unsigned long long end = S.pairs_begin + S.pairs;
+      bool valid = pidx < end;
+      uint2 pr = make_uint2(0, 0);
+      if (valid) {
+        const unsigned long long local = pidx - S.pairs_begin;
+        const uint32_t ia = uint32_t(local / S.right_n);
+        const uint32_t ib = uint32_t(local - (unsigned long long)ia * S.right_n);
+        valid = !(S.tri && ia >= ib);
+        pr = make_uint2(S.left_start + ia, S.right_start + ib);
+      }
+      s_pairs[wib][lane] = pr;
+      ok = valid ? 1u : 0u;
+    }
+    const uint32_t pv = __ballot_sync(kFull, ok != 0u) & 0xFFu;
+    __syncwarp();
+    uint32_t en = 0;
+#pragma unroll
+    for (int q = 0; q < 32; ++q) en |= (((pv >> (q >> 2)) & 1u) & ((sp.b_ops >> (q & 3)) & 1u)) << q;
+    if (en) {
+      PairGenD<W> gen;
+      gen.cv = cv;
+      gen.pairs = s_pairs[wib];
+      PathD<W>::template batch<true>(*cv, gen, 32, en, bw.pend, bw.ids);
+      bw.built += __popc(en);
+    }
+    __syncwarp();
+  }
+  bw.leave(cv);
+}
+
+// Reset the counters of every problem of a step (thread per problem) and the
+// step's work counters.
+static __global__ void k_batch_begin(StepHeader* hdr, const StepProblem* steps, int n_max) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p == 0) hdr->work[0] = hdr->work[1] = hdr->work[2] = 0;
+  if (p >= n_max || p >= hdr->n) return;  // only the step's problems (slots past n are stale)
+  DevCounters* c = steps[p].cv.ctr;
+  c->full = 0;
+  c->solved = 0;
+  c->error = 0;
+  c->defer_n[0] = 0;
+  c->defer_n[1] = 0;
+  c->defer_overflow = 0;
+  c->holes_n = 0;
+  c->built = 0;
+  c->inserted = 0;
+  c->sol = ~0ull;
+}
+
+// Hole fixup of a batch step: warp per (problem, src, dst) move, then each
+// problem's entry count (dense end) is set.
+static __global__ void __launch_bounds__(256) k_batch_fixup(const StepProblem* steps, const uint4* moves, unsigned n,
+                                                            const unsigned* dense_end, int n_problems) {
+  const int lane = threadIdx.x & 31;
+  const unsigned warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (unsigned m = warp; m < n; m += nwarps) {
+    const CacheView& cv = steps[moves[m].x].cv;
+    const unsigned src = moves[m].y, dst = moves[m].z;
+    const uint4* a = cv.arena + size_t(src) * cv.vecs;
+    uint4* b = cv.arena + size_t(dst) * cv.vecs;
+    for (unsigned v = lane; v < cv.vecs; v += 32) b[v] = a[v];
+    if (lane == 0) {
+      cv.prov[dst] = cv.prov[src];
+      const unsigned sp = cv.slotpos[src];
+      cv.slotpos[dst] = sp;
+      const unsigned long long old = cv.table[sp];
+      if (uint32_t(old) == src + 1u) cv.table[sp] = (old & 0xFFFFFFFF00000000ull) | (unsigned long long)(dst + 1u);
+      else atomicExch(&cv.ctr->error, 3u);
+    }
+  }
+}
+
+static __global__ void k_batch_set_entries(const StepProblem* steps, const unsigned* dense_end, int n) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n || dense_end[p] == 0xFFFFFFFFu) return;
+  steps[p].cv.ctr->n_entries = dense_end[p];
+  steps[p].cv.ctr->holes_n = 0;
+}
+
+// ===========================================================================
 // Hole fixup: after a level, move the entries that lie above the level's dense
 // end into the holes below it (one warp per move): copy the CM row, its
 // provenance and slot index, and repoint the table slot to the new id.
@@ -1366,6 +1556,29 @@ cudaError_t Kernels<W>::unary(const CacheView& cv, uint32_t first, uint32_t coun
 template <typename W>
 cudaError_t Kernels<W>::binary(const CacheView& cv, const BinaryPlan& plan, const LaunchCfg& lc) {
   LSYN_DISPATCH(cv.vecs, binary(cv, plan, lc))
+}
+
+template <typename W>
+cudaError_t Kernels<W>::batch_begin(StepHeader* hdr, const StepProblem* steps, int n, const LaunchCfg& lc) {
+  k_batch_begin<<<(std::max(n, 1) + 255) / 256, 256, 0, lc.stream>>>(hdr, steps, n);
+  return cudaGetLastError();
+}
+
+template <typename W>
+cudaError_t Kernels<W>::batch_run(StepHeader* hdr, const StepProblem* steps, const LaunchCfg& lc, int blocks_per_sm) {
+  k_batch_run<W><<<unsigned(lc.sms * std::max(1, blocks_per_sm)), 256, 0, lc.stream>>>(hdr, steps);
+  return cudaGetLastError();
+}
+
+template <typename W>
+cudaError_t Kernels<W>::batch_fixup(const StepProblem* steps, const uint4* moves, unsigned n, const unsigned* dense_end,
+                                    int n_problems, const LaunchCfg& lc) {
+  if (n) {
+    const unsigned blocks = std::max(1u, std::min((n + 7u) / 8u, unsigned(lc.sms * 8)));
+    k_batch_fixup<<<blocks, 256, 0, lc.stream>>>(steps, moves, n, dense_end, n_problems);
+  }
+  k_batch_set_entries<<<(std::max(n_problems, 1) + 255) / 256, 256, 0, lc.stream>>>(steps, dense_end, n_problems);
+  return cudaGetLastError();
 }
 
 template <typename W>

@@ -104,6 +104,30 @@ struct BinaryPlan {
   Split s[kMaxSplits];
 };
 
+// One problem of a batch level step (device array, built by the host per step).
+constexpr int kBatchSplits = 8;  // binary splits of one level: levels up to 17
+
+struct StepProblem {
+  CacheView cv;
+  uint32_t u_first, u_count, u_ops;        // unary work: rows of level k-1
+  uint32_t b_ops, n_splits;                // binary work: splits of level k
+  uint32_t d_n;                            // descriptor work: list length (atoms: n_props)
+  const unsigned long long* d_list;        // NULL: implicit atom descriptors 0..d_n-1
+  unsigned long long u_items_begin;        // prefix over problems, in work items
+  unsigned long long b_items_begin;
+  unsigned long long d_items_begin;
+  Split s[kBatchSplits];
+};
+
+// Header of a batch step: item totals read by the persistent kernels, so one
+// captured graph serves every step.
+struct StepHeader {
+  unsigned long long total_u, total_b, total_d;
+  unsigned long long work[3];  // work-item counters of the three launches
+  int n;                       // problems in this step
+  int pad[3];
+};
+
 // Launch parameters chosen by the host.
 struct LaunchCfg {
   cudaStream_t stream;
@@ -122,6 +146,13 @@ struct Kernels {
   static cudaError_t unary(const CacheView& cv, uint32_t first, uint32_t count, uint32_t ops,
                            const LaunchCfg& lc);
   static cudaError_t binary(const CacheView& cv, const BinaryPlan& plan, const LaunchCfg& lc);
+  // Batch step (problems at their own levels; all use whole warps of vectors):
+  // reset counters, then descriptor (atoms / deferred), unary and binary work.
+  static cudaError_t batch_begin(StepHeader* hdr, const StepProblem* steps, int n, const LaunchCfg& lc);
+  static cudaError_t batch_run(StepHeader* hdr, const StepProblem* steps, const LaunchCfg& lc, int blocks_per_sm);
+  // Moves (problem index, src, dst) of a batch step; then each problem's entry count.
+  static cudaError_t batch_fixup(const StepProblem* steps, const uint4* moves, unsigned n, const unsigned* dense_end,
+                                 int n_problems, const LaunchCfg& lc);
   // Move entries src -> dst (pairs), repointing their table slots.
   static cudaError_t fixup(const CacheView& cv, const uint2* moves, unsigned n, const LaunchCfg& lc);
   // Evaluate a postorder node list on every trace word: scratch [n_nodes][words].

@@ -70,6 +70,10 @@ class lsyn_result(ctypes.Structure):
                 ("formula_cap", ctypes.c_size_t)]
 
 
+class lsyn_batch_tuning(ctypes.Structure):
+    _fields_ = [("blocks_per_sm", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+
+
 class LsynError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"lsyn status {status}: {message}")
@@ -108,6 +112,18 @@ def _load_library():
     lib.lsyn_level_candidates.argtypes = [P(i64), i32, ctypes.c_uint32]
     lib.lsyn_version.restype = ctypes.c_char_p
     lib.lsyn_version.argtypes = []
+    lib.lsyn_batch_create.restype = i32
+    lib.lsyn_batch_create.argtypes = [P(lsyn_problem), i32, P(lsyn_config), P(lsyn_batch_tuning), P(vp)]
+    lib.lsyn_batch_solve.restype = i32
+    lib.lsyn_batch_solve.argtypes = [vp, i32, P(lsyn_result), P(i32)]
+    lib.lsyn_batch_autotune.restype = i32
+    lib.lsyn_batch_autotune.argtypes = [vp, i32, P(lsyn_batch_tuning)]
+    lib.lsyn_batch_problem.restype = i32
+    lib.lsyn_batch_problem.argtypes = [vp, i32, P(vp)]
+    lib.lsyn_batch_last_error.restype = ctypes.c_char_p
+    lib.lsyn_batch_last_error.argtypes = [vp]
+    lib.lsyn_batch_destroy.restype = None
+    lib.lsyn_batch_destroy.argtypes = [vp]
     return lib
 
 
@@ -395,3 +411,96 @@ class Synthesizer:
 
     def formula(self, k: int, index: int) -> str:
         return lsyn_entry_formula(self.ctx, k, index)
+
+
+# ---------------------------------------------------------------------------
+# Batched solving
+# ---------------------------------------------------------------------------
+
+def _batch_err(b) -> str:
+    m = _lib.lsyn_batch_last_error(b)
+    return m.decode() if m else ""
+
+
+def lsyn_batch_create(problems: Sequence[PackedProblem], config: Optional[lsyn_config] = None,
+                      tuning: Optional[lsyn_batch_tuning] = None) -> ctypes.c_void_p:
+    arr = (lsyn_problem * len(problems))(*[p.struct for p in problems])
+    b = ctypes.c_void_p()
+    st = _lib.lsyn_batch_create(arr, len(problems), ctypes.byref(config) if config is not None else None,
+                                ctypes.byref(tuning) if tuning is not None else None, ctypes.byref(b))
+    if st != LSYN_OK:
+        raise LsynError(st, _batch_err(None))
+    return b
+
+
+def lsyn_batch_solve(batch, n: int, max_size: int, formula_cap: int = 4096):
+    """Returns (statuses, results, formulas) for the n problems of the batch."""
+    results = (lsyn_result * n)()
+    bufs = [ctypes.create_string_buffer(formula_cap) for _ in range(n)]
+    for r, buf in zip(results, bufs):
+        r.formula = ctypes.cast(buf, ctypes.c_char_p)
+        r.formula_cap = formula_cap
+    statuses = (ctypes.c_int32 * n)()
+    st = _lib.lsyn_batch_solve(batch, max_size, results, statuses)
+    if st != LSYN_OK:
+        raise LsynError(st, _batch_err(batch))
+    formulas = [bufs[i].value.decode() if statuses[i] == LSYN_OK else None for i in range(n)]
+    return list(statuses), list(results), formulas
+
+
+def lsyn_batch_autotune(batch, max_size: int) -> lsyn_batch_tuning:
+    t = lsyn_batch_tuning()
+    st = _lib.lsyn_batch_autotune(batch, max_size, ctypes.byref(t))
+    if st != LSYN_OK:
+        raise LsynError(st, _batch_err(batch))
+    return t
+
+
+def lsyn_batch_problem(batch, i: int) -> ctypes.c_void_p:
+    ctx = ctypes.c_void_p()
+    _check(_lib.lsyn_batch_problem(batch, i, ctypes.byref(ctx)), None)
+    return ctx
+
+
+def lsyn_batch_destroy(batch) -> None:
+    _lib.lsyn_batch_destroy(batch)
+
+
+class Batch:
+    """Owns a batch: ``with Batch(problems, cfg) as b: statuses, results, formulas = b.solve(13)``."""
+
+    def __init__(self, problems: Sequence[PackedProblem], config: Optional[lsyn_config] = None,
+                 tuning: Optional[lsyn_batch_tuning] = None):
+        self.problems = list(problems)
+        self.config = config
+        self.handle = lsyn_batch_create(self.problems, config, tuning)
+
+    def close(self):
+        if self.handle:
+            lsyn_batch_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def solve(self, max_size: int):
+        return lsyn_batch_solve(self.handle, len(self.problems), max_size)
+
+    def autotune(self, max_size: int) -> lsyn_batch_tuning:
+        return lsyn_batch_autotune(self.handle, max_size)
+
+    def count(self, i: int, k: int) -> int:
+        return lsyn_level_count(lsyn_batch_problem(self.handle, i), k)
+
+    def export(self, i: int, k: int) -> np.ndarray:
+        p = self.problems[i]
+        return lsyn_export_level(lsyn_batch_problem(self.handle, i), k, p.n_traces, p.word_bits)

@@ -1,0 +1,88 @@
+"""Batched solving (lsyn_batch_*) against the plain one-problem path and the
+CPU oracle, through the C ABI (needs a GPU).
+
+Each problem of a batch must give what it gives alone: the same status, the
+same minimal size, a separating formula of that size, and, level by level, the
+same set of characteristic matrices for every level built completely."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2504_18943_gb300 import workloads as W
+from tests.gpu_util import canon, lib, oracle_rows
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    return lib()
+
+
+@pytest.fixture(scope="module")
+def problems():
+    return [W.batched_problem(1000, i, oracle.labeller) for i in range(24)]
+
+
+def _complete_levels(status, res):
+    # the answering level may stop early (solution) or be partial (cache full)
+    return range(1, res.levels_done) if status in (0, -5) else range(1, res.levels_done + 1)
+
+
+def test_batch_equals_plain_path(L, problems):
+    packed = [L.pack_problem(p) for p in problems]
+    cfg = L.make_config(cache_bytes=1 << 30)
+    with L.Batch(packed, cfg) as b:
+        statuses, results, formulas = b.solve(9)
+        for i, p in enumerate(problems):
+            spec = oracle.Spec.from_problem(p)
+            with L.Synthesizer(packed[i], L.make_config(cache_bytes=1 << 30)) as s:
+                st, res, f, _ = s.solve(9)
+                assert statuses[i] == st, (i, statuses[i], st)
+                if st == L.LSYN_OK:
+                    assert results[i].size == res.size, (i, results[i].size, res.size)
+                    assert spec.separates(formulas[i]) and W.formula_size(formulas[i]) == res.size
+                for k in _complete_levels(st, res):
+                    assert np.array_equal(canon(b.export(i, k)), canon(s.export(k))), (i, k)
+    assert any(s == L.LSYN_OK for s in statuses)
+
+
+def test_batch_levels_equal_oracle(L, problems):
+    small = [p for p in problems if p.n_traces <= 120][:4]
+    packed = [L.pack_problem(p) for p in small]
+    with L.Batch(packed, L.make_config(cache_bytes=256 << 20, full_levels=True)) as b:
+        statuses, results, _ = b.solve(4)
+        for i, p in enumerate(small):
+            run = oracle.Spec.from_problem(p).enumerate(results[i].levels_done)
+            for k in range(1, results[i].levels_done + 1):
+                want = canon(oracle_rows(run.cms(k), 64, p.n_traces))
+                assert np.array_equal(canon(b.export(i, k)), want), (i, k)
+
+
+def test_batch_graph_and_autotune(L, problems):
+    packed = [L.pack_problem(p) for p in problems[:12]]
+    cfg = L.make_config(cache_bytes=512 << 20)
+    with L.Batch(packed, cfg) as b:
+        ref = b.solve(8)
+    tuning = L.lsyn_batch_tuning()
+    tuning.blocks_per_sm = 2
+    tuning.use_graph = 1
+    with L.Batch(packed, cfg, tuning) as b:
+        got = b.solve(8)
+        got2 = b.solve(8)  # the captured graph is replayed
+        t = b.autotune(8)
+        got3 = b.solve(8)
+    for g in (got, got2, got3):
+        assert g[0] == ref[0]
+        assert [r.size for r in g[1]] == [r.size for r in ref[1]]
+    assert t.blocks_per_sm in (2, 4, 6, 8) and t.use_graph in (0, 1)
+
+
+def test_batch_rejects_mixed_word_sizes(L, problems):
+    a = L.pack_problem(problems[0])
+    p = problems[1]
+    b32 = L.pack_traces(p.traces.bits, p.traces.lengths, p.n_pos, p.n_neg, 64)
+    b32 = L.PackedProblem(b32.n_props, b32.n_pos, b32.n_neg, 32, b32.lengths, b32.atom_words.astype(np.uint32))
+    with pytest.raises(L.LsynError) as ei:
+        L.Batch([a, b32])
+    assert ei.value.status == L.LSYN_E_INVAL
