@@ -238,24 +238,57 @@ lsyn_status lsyn_eval(const lsyn_problem* problem, const char* formula, void* ds
                       const lsyn_config* config);
 
 /*
- * Batched solving: many independent specifications enumerated together, one
- * persistent launch per step over a packed work list of every unfinished
- * problem, each at its own level (the listing of "A generic program
- * synthesiser" applied to each problem; batching is this library's own).
- *   problems   host array of n problem descriptions (same word_bits for all);
- *              copied during the call.
- *   config     shared by every problem; cache_bytes is PER PROBLEM. Device
- *              memory of all problems stays allocated until lsyn_batch_destroy.
- *   tuning     launch shape (NULL = defaults: 4 blocks per SM, no graph).
- * Errors: as lsyn_create (the first failing problem is named in
- * lsyn_batch_last_error(NULL)).
+ * Multi-problem scheduling (batches and the server). The paper enumerates one
+ * specification at a time; this library also advances many at once, each at
+ * its own level, in one persistent launch per step over a packed work list of
+ * every admitted problem (the listing of "A generic program synthesiser"
+ * applied to each problem).
+ *
+ * Memory: per-problem language caches live in one device memory pool
+ * (pool_bytes). A cache starts small and grows before each level to the
+ * entries the level is predicted to add, without copying (virtual address
+ * ranges backed on demand), up to the same entry limit lsyn_create derives
+ * from config->cache_bytes. So each problem's levels, status and answer size
+ * are those of lsyn_create + lsyn_solve with the same config, whatever else
+ * runs beside it; only which separating formula of the minimal size is
+ * returned may differ. A level that outgrows its prediction is undone and run
+ * again with room for every candidate. When the pool cannot hold a problem's
+ * next level it waits; when nothing can run, the most recently admitted
+ * problems are evicted (their caches dropped, restarted later). A problem that
+ * does not fit even alone is capped at what the pool gives it and answers
+ * LSYN_E_CACHE_FULL (its error text says so).
  */
-typedef struct lsyn_batch lsyn_batch;
 typedef struct {
   int32_t blocks_per_sm;  /* persistent blocks of 256 threads per SM (0 = 4) */
-  int32_t use_graph;      /* 1: replay the step (upload, reset, launch, copy back) from a CUDA graph */
-  int32_t reserved[2];
+  int32_t use_graph;      /* 1: replay the step (upload, reset, launch, copy back) from CUDA graphs */
+  int32_t max_active;     /* problems admitted at once (0: a batch admits all, a server 256) */
+  int32_t predict_pct;    /* a level's predicted new entries: candidates x this percentage of the
+                             previous level's unique ratio (0 = 150); lower saves memory, costs redos */
+  uint64_t pool_bytes;    /* device memory for every cache together (0: 90% of the free memory) */
+  uint64_t solo_candidates; /* a level with more candidates runs as launches of its own with the
+                               one-problem kernels inside the step (0 = 2^19) */
 } lsyn_batch_tuning;
+
+typedef struct {
+  int64_t submitted, completed, active, queued;
+  int64_t steps;          /* batch steps run */
+  int64_t evictions;      /* problems evicted and restarted for lack of memory */
+  int64_t redos;          /* levels undone and run again (outgrew their prediction) */
+  int64_t reserved0;
+  uint64_t pool_bytes, pool_in_use, pool_peak;
+} lsyn_sched_stats;
+
+/*
+ * Batched solving of n independent specifications.
+ *   problems   host array of n problem descriptions (32- and 64-bit words may
+ *              be mixed); copied during the call.
+ *   config     shared by every problem; cache_bytes is each problem's cap.
+ *   tuning     NULL = defaults.
+ * Errors: as lsyn_create (the first failing problem is named in
+ * lsyn_batch_last_error(NULL)); LSYN_E_CUDA if the driver's virtual-memory
+ * interface is unavailable.
+ */
+typedef struct lsyn_batch lsyn_batch;
 
 lsyn_status lsyn_batch_create(const lsyn_problem* problems, int32_t n, const lsyn_config* config,
                               const lsyn_batch_tuning* tuning, lsyn_batch** out);
@@ -265,31 +298,81 @@ lsyn_status lsyn_batch_create(const lsyn_problem* problems, int32_t n, const lsy
  * with its own caller-owned formula buffer) receive what lsyn_solve would
  * return, ms = time from the start of this call to the problem's answer;
  * statuses[i] receives the status lsyn_solve would return for problem i
- * (LSYN_OK, LSYN_NOT_FOUND, LSYN_E_CACHE_FULL). The call itself returns
+ * (LSYN_OK, LSYN_NOT_FOUND, LSYN_E_CACHE_FULL; LSYN_E_NOMEM if the pool cannot
+ * hold even its constants). Caches of answered problems stay on the device for
+ * lsyn_batch_problem until their memory is needed. The call itself returns
  * LSYN_OK unless a CUDA error or a consistency check stops the whole batch.
  */
 lsyn_status lsyn_batch_solve(lsyn_batch* batch, int32_t max_size, lsyn_result* results, int32_t* statuses);
 
 /*
  * Autotuner: solves the batch (up to max_size) once per candidate launch shape
- * (blocks per SM in {2, 4, 6, 8}, with and without the step graph), keeps the
+ * (blocks per SM in {2, 4, 6, 8}, with and without the step graphs), keeps the
  * fastest for later lsyn_batch_solve calls and writes it to *out (may be NULL).
  */
 lsyn_status lsyn_batch_autotune(lsyn_batch* batch, int32_t max_size, lsyn_batch_tuning* out);
 
 /*
  * Problem i of the batch as a context handle owned by the batch (valid until
- * lsyn_batch_destroy; do not pass it to lsyn_destroy). Read-only calls
+ * lsyn_batch_destroy; lsyn_destroy ignores it). Read-only calls
  * (lsyn_level_count, lsyn_export_level, lsyn_entry_formula) inspect the levels
- * the batch built for that problem.
+ * the last lsyn_batch_solve built for that problem while its cache is
+ * resident (otherwise they see no levels); driving calls answer LSYN_E_STATE.
  */
 lsyn_status lsyn_batch_problem(lsyn_batch* batch, int32_t i, lsyn_ctx** out);
+
+lsyn_status lsyn_batch_stats(const lsyn_batch* batch, lsyn_sched_stats* out);
 
 /* Message of the last error of the batch (NULL: of the last failed lsyn_batch_create on this thread). */
 const char* lsyn_batch_last_error(const lsyn_batch* batch);
 
 /* Release the batch and every problem's device memory. NULL is allowed. */
 void lsyn_batch_destroy(lsyn_batch* batch);
+
+/*
+ * Serving: a host thread runs the step loop over the problems submitted so
+ * far. A submission joins the loop between steps as soon as a slot and pool
+ * memory allow (admission in submission order, by the memory the running
+ * problems are predicted to need next plus what the newcomer needs first), so
+ * problems arriving while others are on the GPU share their launches
+ * (continuous batching). Results are collected by ticket.
+ *   config   per-problem settings as for a batch (cache_bytes = each cap).
+ *   tuning   NULL = defaults (256 problems at once, 90% of free memory).
+ * Thread safety: every lsyn_server_* call, lsyn_submit, lsyn_poll and
+ * lsyn_wait may be made from any host thread.
+ */
+typedef struct lsyn_server lsyn_server;
+
+lsyn_status lsyn_server_create(const lsyn_config* config, const lsyn_batch_tuning* tuning, lsyn_server** out);
+
+/*
+ * Queue a problem (copied during the call) to be solved up to max_size
+ * (1..17). *ticket names it for lsyn_poll / lsyn_wait. Errors: LSYN_E_INVAL
+ * (invalid problem or max_size; nothing is queued), LSYN_E_STATE (the server
+ * stopped after an error).
+ */
+lsyn_status lsyn_submit(lsyn_server* server, const lsyn_problem* problem, int32_t max_size, uint64_t* ticket);
+
+/*
+ * LSYN_PENDING while the problem waits or runs. Once it is answered: its
+ * status (as lsyn_solve's: LSYN_OK, LSYN_NOT_FOUND, LSYN_E_CACHE_FULL, or an
+ * error), with *out filled as lsyn_solve fills it (formula into
+ * out->formula / formula_cap; ms = time from submission to the answer, queueing
+ * included); the ticket is then retired. LSYN_E_INVAL for an unknown or
+ * retired ticket, or if out->formula is too small (the result is kept).
+ */
+lsyn_status lsyn_poll(lsyn_server* server, uint64_t ticket, lsyn_result* out);
+
+/* As lsyn_poll, but waits up to timeout_ms (< 0: no limit); LSYN_E_TIMEOUT if still pending. */
+lsyn_status lsyn_wait(lsyn_server* server, uint64_t ticket, int32_t timeout_ms, lsyn_result* out);
+
+lsyn_status lsyn_server_stats(lsyn_server* server, lsyn_sched_stats* out);
+
+/* Message of the server's last error (NULL: of the last failed lsyn_server_create on this thread). */
+const char* lsyn_server_last_error(const lsyn_server* server);
+
+/* Stop the loop (running problems are dropped) and release everything. NULL is allowed. */
+void lsyn_server_destroy(lsyn_server* server);
 
 /*
  * Formula evaluation that allocates no device memory (the paper has no

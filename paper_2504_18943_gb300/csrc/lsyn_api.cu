@@ -284,6 +284,21 @@ void pack_host(const lsyn_problem* p, const Layout& L, unsigned vecs, std::vecto
 }  // namespace
 
 
+bool lsyn::cache_sizing(unsigned long long cache_bytes, size_t M, double load, unsigned long long* table_cap,
+                        unsigned long long* entries) {
+  unsigned long long best_cap = 0, best_e = 0;
+  for (unsigned long long cap = 1024; cap <= (1ull << 32); cap <<= 1) {
+    if (cap * 8 >= cache_bytes) break;
+    unsigned long long e = (cache_bytes - cap * 8) / (M + kEntryMetaBytes);
+    e = std::min<unsigned long long>(e, (unsigned long long)(double(cap) * load));
+    e = std::min<unsigned long long>(e, kMaxEntries);
+    if (e > best_e) { best_e = e; best_cap = cap; }
+  }
+  *table_cap = best_cap;
+  *entries = best_e;
+  return best_e >= 64;
+}
+
 uint32_t lsyn::plan_hole_moves(const uint2* holes, unsigned n, uint32_t start, uint32_t total,
                                std::vector<uint2>* mv) {
   std::vector<std::pair<uint32_t, uint32_t>> rng;
@@ -402,6 +417,13 @@ lsyn_status lsyn::ctx_commit_level(lsyn_ctx* c, int k, const DevCounters& h, uin
   return LSYN_OK;
 }
 
+int64_t lsyn::level_candidate_count(const lsyn_ctx* c, int k) {
+  if (k == 1) return c->n_props;
+  std::vector<int64_t> sizes(c->level_n.begin() + 1, c->level_n.end());
+  if (int(sizes.size()) < k - 1) return 0;
+  return level_candidates(sizes.data(), k, c->op_mask);
+}
+
 extern "C" {
 
 const char* lsyn_version(void) { return "lsyn 0.1 (sm_103a)"; }
@@ -416,7 +438,7 @@ const char* lsyn_last_error(const lsyn_ctx* ctx) {
 }
 
 void lsyn_destroy(lsyn_ctx* c) {
-  if (!c) return;
+  if (!c || c->borrowed) return;  // a borrowed handle belongs to its batch or server
   int prev = -1;
   cudaGetDevice(&prev);
   cudaSetDevice(c->device);
@@ -425,9 +447,11 @@ void lsyn_destroy(lsyn_ctx* c) {
   if (c->events_ready)
     for (auto& e : c->ev) if (e) cudaEventDestroy(e);
   c->mem.release_all();
-  if (c->h_snap) cudaFreeHost(c->h_snap);
-  if (c->h_fbuf) cudaFreeHost(c->h_fbuf);
-  if (c->h_fstatus) cudaFreeHost(c->h_fstatus);
+  if (c->owns_host) {
+    if (c->h_snap) cudaFreeHost(c->h_snap);
+    if (c->h_fbuf) cudaFreeHost(c->h_fbuf);
+    if (c->h_fstatus) cudaFreeHost(c->h_fstatus);
+  }
   if (prev >= 0) cudaSetDevice(prev);
   delete c;
 }
@@ -438,8 +462,8 @@ lsyn_status lsyn_create(const lsyn_problem* problem, const lsyn_config* config, 
 
 }  // extern "C"
 
-lsyn_status lsyn::ctx_create(const lsyn_problem* problem, const lsyn_config* config, bool warp_layout,
-                             lsyn_ctx** out) {
+lsyn_status lsyn::ctx_shell(const lsyn_problem* problem, const lsyn_config* config, bool warp_layout,
+                            lsyn_ctx** out, std::vector<uint32_t>* consts, std::vector<uint32_t>* atoms) {
   g_create_error.clear();
   if (!out) { g_create_error = "out is NULL"; return LSYN_E_INVAL; }
   *out = nullptr;
@@ -471,23 +495,18 @@ lsyn_status lsyn::ctx_create(const lsyn_problem* problem, const lsyn_config* con
     return LSYN_E_UNSUPPORTED;
   }
   const size_t M = size_t(vecs) * 16;
-  // Hash-table capacity (a power of two) and arena entries within the budget,
-  // at most `load` slots in use.
   unsigned long long best_cap = 0, best_e = 0;
-  for (unsigned long long cap = 1024; cap <= (1ull << 34); cap <<= 1) {
-    if (cap * 8 >= cache_bytes) break;
-    unsigned long long e = (cache_bytes - cap * 8) / (M + 12);
-    e = std::min<unsigned long long>(e, (unsigned long long)(double(cap) * load));
-    e = std::min<unsigned long long>(e, kMaxEntries);
-    if (e > best_e) { best_e = e; best_cap = cap; }
+  if (!cache_sizing(cache_bytes, M, load, &best_cap, &best_e)) {
+    g_create_error = "cache_bytes too small";
+    return LSYN_E_INVAL;
   }
-  if (best_e < 64) { g_create_error = "cache_bytes too small"; return LSYN_E_INVAL; }
 
   lsyn_ctx* c = new (std::nothrow) lsyn_ctx;
   if (!c) { g_create_error = "out of host memory"; return LSYN_E_NOMEM; }
   c->op_mask = mask;
   c->full_levels = cfg.full_levels != 0;
   c->timing = cfg.timing != 0;
+  c->table_load = load;
   c->mem.alloc = cfg.alloc;
   c->mem.free = cfg.free;
   c->mem.user = cfg.alloc_user;
@@ -506,21 +525,38 @@ lsyn_status lsyn::ctx_create(const lsyn_problem* problem, const lsyn_config* con
   c->defer_cap = unsigned(std::max(1ull << 16, std::min(1ull << 23, best_e / 16)));
   c->hole_cap = 1u << 16;
   c->move_cap = c->hole_cap * 32u;
+  cudaError_t e;
+  if (cfg.device >= 0 && (e = cudaSetDevice(cfg.device)) != cudaSuccess) {
+    delete c;
+    g_create_error = cudaGetErrorString(e);
+    return LSYN_E_CUDA;
+  }
+  if ((e = cudaGetDevice(&c->device)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device)) != cudaSuccess) {
+    delete c;
+    g_create_error = cudaGetErrorString(e);
+    return LSYN_E_CUDA;
+  }
+  if (consts && atoms) pack_host(problem, L, vecs, consts, atoms);
+  c->level_start.assign(1, 0);
+  c->level_n.assign(1, 0);
+  *out = c;
+  return LSYN_OK;
+}
 
+lsyn_status lsyn::ctx_create(const lsyn_problem* problem, const lsyn_config* config, bool warp_layout,
+                             lsyn_ctx** out) {
+  std::vector<uint32_t> consts, atoms;
+  lsyn_ctx* c = nullptr;
+  lsyn_status s = ctx_shell(problem, config, warp_layout, &c, &consts, &atoms);
+  if (s != LSYN_OK) return s;
+  const size_t M = size_t(c->vecs) * 16;
   auto bail = [&](lsyn_status st, const std::string& msg) {
     g_create_error = msg;
     lsyn_destroy(c);
     return st;
   };
   cudaError_t e;
-  if (cfg.device >= 0) {
-    if ((e = cudaSetDevice(cfg.device)) != cudaSuccess) return bail(LSYN_E_CUDA, cudaGetErrorString(e));
-  }
-  if ((e = cudaGetDevice(&c->device)) != cudaSuccess) return bail(LSYN_E_CUDA, cudaGetErrorString(e));
-  cudaDeviceProp prop;
-  if ((e = cudaGetDeviceProperties(&prop, c->device)) != cudaSuccess) return bail(LSYN_E_CUDA, cudaGetErrorString(e));
-  c->sms = prop.multiProcessorCount;
-
   c->arena = static_cast<uint4*>(c->mem.get(size_t(c->max_entries) * M));
   c->prov = static_cast<unsigned long long*>(c->mem.get(size_t(c->max_entries) * 8));
   c->table = static_cast<unsigned long long*>(c->mem.get(size_t(c->table_cap) * 8));
@@ -530,12 +566,13 @@ lsyn_status lsyn::ctx_create(const lsyn_problem* problem, const lsyn_config* con
   c->defer[0] = static_cast<unsigned long long*>(c->mem.get(size_t(c->defer_cap) * 8));
   c->defer[1] = static_cast<unsigned long long*>(c->mem.get(size_t(c->defer_cap) * 8));
   c->slotpos = static_cast<unsigned*>(c->mem.get(size_t(c->max_entries) * 4));
+  c->homes = static_cast<unsigned*>(c->mem.get(size_t(c->max_entries) * 4));
   c->holes = static_cast<uint2*>(c->mem.get(size_t(c->hole_cap) * sizeof(uint2)));
   c->moves = static_cast<uint2*>(c->mem.get(size_t(c->move_cap) * sizeof(uint2)));
   c->fbuf = static_cast<char*>(c->mem.get(lsyn_ctx::kFormulaCap));
   c->fstatus = static_cast<int*>(c->mem.get(sizeof(int)));
   if (!c->arena || !c->prov || !c->table || !c->ctr || !c->consts || !c->atoms || !c->defer[0] || !c->defer[1] ||
-      !c->fbuf || !c->fstatus || !c->slotpos || !c->holes || !c->moves)
+      !c->fbuf || !c->fstatus || !c->slotpos || !c->homes || !c->holes || !c->moves)
     return bail(LSYN_E_NOMEM, "device allocation failed");
   if (cudaMallocHost(&c->h_snap, sizeof(Snap) * lsyn_ctx::kSnaps) != cudaSuccess ||
       cudaMallocHost(&c->h_fbuf, lsyn_ctx::kFormulaCap) != cudaSuccess ||
@@ -543,12 +580,11 @@ lsyn_status lsyn::ctx_create(const lsyn_problem* problem, const lsyn_config* con
     cudaGetLastError();
     return bail(LSYN_E_NOMEM, "pinned host allocation failed");
   }
+  c->owns_host = true;
   for (auto& ev : c->ev)
     if ((e = cudaEventCreate(&ev)) != cudaSuccess) return bail(LSYN_E_CUDA, cudaGetErrorString(e));
   c->events_ready = true;
 
-  std::vector<uint32_t> consts, atoms;
-  pack_host(problem, L, vecs, &consts, &atoms);
   e = cudaMemcpyAsync(c->consts, consts.data(), consts.size() * 4, cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(c->atoms, atoms.data(), atoms.size() * 4, cudaMemcpyHostToDevice, c->stream);
@@ -564,6 +600,7 @@ extern "C" {
 
 lsyn_status lsyn_reset(lsyn_ctx* c) {
   if (!c) return LSYN_E_INVAL;
+  if (c->borrowed) return c->fail(LSYN_E_STATE, "a batch or server problem is driven by its owner");
   cudaSetDevice(c->device);
   cudaError_t e = cudaMemsetAsync(c->table, 0, size_t(c->table_cap) * 8, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->ctr, 0, sizeof(DevCounters), c->stream);
@@ -579,6 +616,7 @@ lsyn_status lsyn_reset(lsyn_ctx* c) {
 
 lsyn_status lsyn_enumerate_level(lsyn_ctx* c, int32_t k, lsyn_level_stats* out) {
   if (!c) return LSYN_E_INVAL;
+  if (c->borrowed) return c->fail(LSYN_E_STATE, "a batch or server problem is driven by its owner");
   if (k != c->levels_done + 1) return c->fail(LSYN_E_STATE, "level k must be levels_done + 1");
   if (c->last_incomplete) return c->fail(LSYN_E_STATE, "the previous level is incomplete (cache full or stopped early)");
   if (k > 64) return c->fail(LSYN_E_INVAL, "levels above 64 are not supported");
@@ -727,6 +765,7 @@ lsyn_status lsyn_enumerate_level(lsyn_ctx* c, int32_t k, lsyn_level_stats* out) 
 
 lsyn_status lsyn_solve(lsyn_ctx* c, int32_t max_size, lsyn_result* out) {
   if (!c || !out) return LSYN_E_INVAL;
+  if (c->borrowed) return c->fail(LSYN_E_STATE, "a batch or server problem is driven by its owner");
   if (max_size < 1 || max_size > 64) return c->fail(LSYN_E_INVAL, "max_size must be in 1..64");
   const double t0 = now_ms();
   out->found = 0;

@@ -77,6 +77,14 @@ struct LevelPlan {
   double op_bytes_unary = 0, op_bytes_binary = 0;
 };
 
+// Language-cache sizing for a byte budget: the hash-table capacity (a power of
+// two, at most `load` of it in use) and the arena entries that fit beside it.
+// Per entry the cache holds the CM (M bytes), its provenance (8), its table
+// slot (4) and its hash's low word (4). Returns false if fewer than 64 fit.
+bool cache_sizing(unsigned long long cache_bytes, size_t M, double load, unsigned long long* table_cap,
+                  unsigned long long* entries);
+constexpr size_t kEntryMetaBytes = 16;
+
 // Hole moves: the id ranges [x, y) reserved in [start, total) but left unused
 // by warps; returns the level's dense end and the (src, dst) moves that fill
 // the holes below it with the entries above it.
@@ -95,6 +103,9 @@ struct lsyn_ctx {
   uint32_t op_mask = LSYN_OPS_ALL;
   bool full_levels = false;
   bool timing = false;
+  bool borrowed = false;   // owned by a batch or server: not driven or destroyed through the handle
+  bool owns_host = false;  // h_snap / h_fbuf / h_fstatus are this context's pinned buffers
+  double table_load = 0.5;
   // problem
   int n_props = 0, n_pos = 0, n_neg = 0, T = 0, word_bits = 32, max_len = 1, steps = 0;
   unsigned vecs = 0;
@@ -112,6 +123,7 @@ struct lsyn_ctx {
   unsigned long long* defer[2] = {nullptr, nullptr};
   unsigned defer_cap = 0;
   unsigned* slotpos = nullptr;  // [max_entries]
+  unsigned* homes = nullptr;    // [max_entries]
   uint2* holes = nullptr;       // [hole_cap]
   unsigned hole_cap = 0;
   uint2* moves = nullptr;       // [move_cap]
@@ -161,6 +173,7 @@ struct lsyn_ctx {
     cv.defer_out_n = defer_out_n;
     cv.defer_cap = defer_cap;
     cv.slotpos = slotpos;
+    cv.homes = homes;
     cv.holes = holes;
     cv.hole_cap = hole_cap;
     cv.chunk = chunk;
@@ -175,6 +188,13 @@ namespace lsyn {
 // Create a context; warp_layout forces whole warps of 16-byte vectors (the
 // batch kernels need it).
 lsyn_status ctx_create(const lsyn_problem* problem, const lsyn_config* config, bool warp_layout, lsyn_ctx** out);
+// Validate a problem and fill a context's layout and sizing (max_entries and
+// table_cap follow cache_bytes as in ctx_create) without device memory; the
+// padded constants and atom rows are packed into `consts` / `atoms` if given.
+lsyn_status ctx_shell(const lsyn_problem* problem, const lsyn_config* config, bool warp_layout, lsyn_ctx** out,
+                      std::vector<uint32_t>* consts, std::vector<uint32_t>* atoms);
+// Candidates level k builds given the sizes of levels 1..k-1 (sizes[i-1]).
+int64_t level_candidate_count(const lsyn_ctx* c, int k);
 // The plan of level k (= levels_done + 1); also sets the id chunk size.
 void ctx_level_plan(lsyn_ctx* c, int k, LevelPlan* lp);
 // Record level k from its final counters (after deferred passes and fixup):

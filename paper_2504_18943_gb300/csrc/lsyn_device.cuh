@@ -268,6 +268,7 @@ struct PathA {
         for (int v = 0; v < V; ++v) dst[v] = c[v];
         cv.prov[id] = desc;
         cv.slotpos[id] = unsigned(pos);
+        cv.homes[id] = uint32_t(h);
         st_release(slot, tag | (unsigned long long)(id + 1u));  // orders this thread's CM and provenance first
         return 1;
       }
@@ -653,6 +654,7 @@ struct PathC {
         if (my_id < cv.max_entries) {
           cv.prov[my_id] = my_desc;
           cv.slotpos[my_id] = unsigned(pos);
+          cv.homes[my_id] = uint32_t(h);
           pend.slot = slot;
           pend.val = tag | (unsigned long long)(my_id + 1u);
         } else {
@@ -1020,6 +1022,7 @@ struct PathD {
         if (my_id < cv.max_entries) {
           cv.prov[my_id] = my_desc;
           cv.slotpos[my_id] = unsigned(pos);
+          cv.homes[my_id] = uint32_t(h);
           pend.slot = slot;
           pend.val = tag | (unsigned long long)(my_id + 1u);
         } else {
@@ -1247,54 +1250,113 @@ __device__ __forceinline__ unsigned long long grab(unsigned long long* counter) 
   return __shfl_sync(kFull, it, 0);
 }
 
+// Path A inside the batch runner (CMs of at most 8 vectors): every lane holds
+// one candidate, named by its descriptor, rebuilds it from its operands and
+// probes / inserts it alone, exactly as k_unary_a / k_binary_a / k_desc_a do.
+// The problem's constants sit in this warp's shared slot `ca`, laid out as
+// PathA<W, V>::Consts.
+template <typename W, int V>
+__device__ __forceinline__ unsigned batch_a_one(const CacheView& cv, const uint4* ca, uint64_t d) {
+  const auto& s = *reinterpret_cast<const typename PathA<W, V>::Consts*>(ca);
+  uint4 c[V];
+  rebuild_a<W, V>(cv, s, d, c);
+  return PathA<W, V>::process(cv, s, c, d, ld_relaxed_u32(&cv.ctr->full) != 0u);
+}
+
+template <typename W>
+__device__ __forceinline__ void batch_a_load(const CacheView& cv, uint4* ca) {
+  const unsigned V = cv.vecs;
+  for (unsigned i = threadIdx.x & 31; i < V; i += 32) {
+    ca[i] = cv.lenmask[i];
+    ca[V + i] = cv.label[i];
+    ca[2 * V + i] = cv.care[i];
+    ca[3 * V + i] = cv.hkey[i];
+    ca[4 * V + i] = cv.hmul[i];
+  }
+  __syncwarp();
+}
+
+// Every lane with `on` set settles descriptor d; returns the warp's inserts.
+template <typename W>
+__device__ unsigned batch_a(const CacheView& cv, const uint4* ca, uint64_t d, bool on) {
+  unsigned ins = 0;
+  if (on) {
+    switch (cv.vecs) {
+      case 1: ins = batch_a_one<W, 1>(cv, ca, d); break;
+      case 2: ins = batch_a_one<W, 2>(cv, ca, d); break;
+      case 4: ins = batch_a_one<W, 4>(cv, ca, d); break;
+      default: ins = batch_a_one<W, 8>(cv, ca, d); break;
+    }
+  }
+  return __reduce_add_sync(kFull, ins);
+}
+
 template <typename W>
 __global__ void __launch_bounds__(256) k_batch_run(StepHeader* hdr, const StepProblem* steps) {
   __shared__ CacheView s_cv[8];
   __shared__ uint2 s_pairs[8][8];
   __shared__ uint64_t s_d[8][32];
+  __shared__ uint4 s_ca[8][40];  // path-A constants of the warp's problem (5 x up to 8 vectors)
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   CacheView* cv = &s_cv[wib];
+  uint4* ca = s_ca[wib];
   const int n = hdr->n;
   BatchWarp<W> bw;
+  auto enter = [&](int p) {
+    const bool fresh = p != bw.cur;
+    bw.enter(steps, p, cv);
+    if (fresh && cv->vecs <= 8u) batch_a_load<W>(*cv, ca);
+  };
   // 1. descriptors: atoms of problems at level 1, deferred re-examination
   for (unsigned long long it = grab(&hdr->work[0]); it < hdr->total_d; it = grab(&hdr->work[0])) {
     const int p = find_problem(steps, n, it, 0);
-    bw.enter(steps, p, cv);
+    enter(p);
     const StepProblem& sp = steps[p];
     const uint32_t base = uint32_t(it - sp.d_items_begin) * 32u;
     const uint32_t cnt = min(32u, sp.d_n - base);
-    s_d[wib][lane] = lane < int(cnt) ? (sp.d_list ? sp.d_list[base + lane] : pack_desc(kAtom, base + lane, 0))
-                                     : pack_desc(kAtom, 0, 0);
-    __syncwarp();
-    ListGenD<W> gen;
-    gen.cv = cv;
-    gen.d = s_d[wib];
-    PathD<W>::template batch<false>(*cv, gen, int(cnt), cnt >= 32u ? 0xFFFFFFFFu : ((1u << cnt) - 1u), bw.pend,
-                                    bw.ids);
+    const uint64_t d = lane < int(cnt) ? (sp.d_list ? sp.d_list[base + lane] : pack_desc(kAtom, base + lane, 0))
+                                       : pack_desc(kAtom, 0, 0);
+    if (cv->vecs <= 8u) {
+      bw.ids.inserted += batch_a<W>(*cv, ca, d, lane < int(cnt));
+    } else {
+      s_d[wib][lane] = d;
+      __syncwarp();
+      ListGenD<W> gen;
+      gen.cv = cv;
+      gen.d = s_d[wib];
+      PathD<W>::template batch<false>(*cv, gen, int(cnt), cnt >= 32u ? 0xFFFFFFFFu : ((1u << cnt) - 1u), bw.pend,
+                                      bw.ids);
+    }
     if (!sp.d_list) bw.built += cnt;  // atoms count as built; deferred ones were counted when first built
     __syncwarp();
   }
   // 2. unary operators, 8 rows (32 candidates) per item
   for (unsigned long long it = grab(&hdr->work[1]); it < hdr->total_u; it = grab(&hdr->work[1])) {
     const int p = find_problem(steps, n, it, 1);
-    bw.enter(steps, p, cv);
+    enter(p);
     if (__any_sync(kFull, stop_requested(*cv))) continue;
     const StepProblem& sp = steps[p];
     const uint32_t base = uint32_t(it - sp.u_items_begin) * 8u;
     const uint32_t nrows = min(8u, sp.u_count - base);
-    RowGenD<W> gen;
-    gen.cv = cv;
-    gen.id0 = sp.u_first + base;
     uint32_t en = 0;
 #pragma unroll
     for (int q = 0; q < 32; ++q) en |= ((sp.u_ops >> (q & 3)) & 1u & (uint32_t(q >> 2) < nrows ? 1u : 0u)) << q;
-    PathD<W>::template batch<false>(*cv, gen, int(4 * nrows), en, bw.pend, bw.ids);
+    if (cv->vecs <= 8u) {
+      const uint32_t opc[4] = {kNot, kNext, kFuture, kGlobally};
+      const uint64_t d = pack_desc(opc[lane & 3], sp.u_first + base + uint32_t(lane >> 2), 0);
+      bw.ids.inserted += batch_a<W>(*cv, ca, d, (en >> lane) & 1u);
+    } else {
+      RowGenD<W> gen;
+      gen.cv = cv;
+      gen.id0 = sp.u_first + base;
+      PathD<W>::template batch<false>(*cv, gen, int(4 * nrows), en, bw.pend, bw.ids);
+    }
     bw.built += __popc(en);
   }
   // 3. binary operators, 8 pairs (32 candidates) per item
   for (unsigned long long it = grab(&hdr->work[2]); it < hdr->total_b; it = grab(&hdr->work[2])) {
     const int p = find_problem(steps, n, it, 2);
-    bw.enter(steps, p, cv);
+    enter(p);
     if (__any_sync(kFull, stop_requested(*cv))) continue;
     const StepProblem& sp = steps[p];
     const unsigned long long g0 = (it - sp.b_items_begin) * 8ull;
@@ -1323,10 +1385,19 @@ __global__ void __launch_bounds__(256) k_batch_run(StepHeader* hdr, const StepPr
 #pragma unroll
     for (int q = 0; q < 32; ++q) en |= (((pv >> (q >> 2)) & 1u) & ((sp.b_ops >> (q & 3)) & 1u)) << q;
     if (en) {
-      PairGenD<W> gen;
-      gen.cv = cv;
-      gen.pairs = s_pairs[wib];
-      PathD<W>::template batch<true>(*cv, gen, 32, en, bw.pend, bw.ids);
+      if (cv->vecs <= 8u) {
+        const uint2 pr = s_pairs[wib][lane >> 2];
+        const int o = lane & 3;  // and, or, U(a, b), U(b, a)
+        const uint64_t d = o == 0 ? pack_desc(kAnd, pr.x, pr.y)
+                         : o == 1 ? pack_desc(kOr, pr.x, pr.y)
+                         : o == 2 ? pack_desc(kUntil, pr.x, pr.y) : pack_desc(kUntil, pr.y, pr.x);
+        bw.ids.inserted += batch_a<W>(*cv, ca, d, (en >> lane) & 1u);
+      } else {
+        PairGenD<W> gen;
+        gen.cv = cv;
+        gen.pairs = s_pairs[wib];
+        PathD<W>::template batch<true>(*cv, gen, 32, en, bw.pend, bw.ids);
+      }
       bw.built += __popc(en);
     }
     __syncwarp();
@@ -1351,6 +1422,7 @@ static __global__ void k_batch_begin(StepHeader* hdr, const StepProblem* steps, 
   c->built = 0;
   c->inserted = 0;
   c->sol = ~0ull;
+  for (int i = 0; i < 8; ++i) c->work[i] = 0;  // tile counters of one-problem launches in the step
 }
 
 // Hole fixup of a batch step: warp per (problem, src, dst) move, then each
@@ -1368,6 +1440,7 @@ static __global__ void __launch_bounds__(256) k_batch_fixup(const StepProblem* s
     for (unsigned v = lane; v < cv.vecs; v += 32) b[v] = a[v];
     if (lane == 0) {
       cv.prov[dst] = cv.prov[src];
+      cv.homes[dst] = cv.homes[src];
       const unsigned sp = cv.slotpos[src];
       cv.slotpos[dst] = sp;
       const unsigned long long old = cv.table[sp];
@@ -1400,12 +1473,43 @@ static __global__ void __launch_bounds__(256) k_fixup(CacheView cv, const uint2*
     for (unsigned v = lane; v < cv.vecs; v += 32) b[v] = a[v];
     if (lane == 0) {
       cv.prov[dst] = cv.prov[src];
+      cv.homes[dst] = cv.homes[src];
       const unsigned sp = cv.slotpos[src];
       cv.slotpos[dst] = sp;
       const unsigned long long old = cv.table[sp];
       if (uint32_t(old) == src + 1u) cv.table[sp] = (old & 0xFFFFFFFF00000000ull) | (unsigned long long)(dst + 1u);
       else atomicExch(&cv.ctr->error, 3u);
     }
+  }
+}
+
+// ===========================================================================
+// Table rebuild: re-insert the published slots of entries below live_end into
+// a cleared table of any capacity. An entry's home slot comes from the low
+// word of its hash (homes[]), so no CM is read; tags move unchanged. Slots of
+// entries at or above live_end (a level being undone), tombstones and pending
+// claims are dropped.
+// ===========================================================================
+static __global__ void __launch_bounds__(256) k_rehash(const unsigned long long* old_t, unsigned long long old_cap,
+                                                       unsigned long long* new_t, unsigned long long new_mask,
+                                                       const unsigned* homes, unsigned* slotpos, unsigned live_end,
+                                                       unsigned* error) {
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < old_cap; i += stride) {
+    const unsigned long long v = old_t[i];
+    const uint32_t low = uint32_t(v);
+    if (v == 0ull || low >= kSlotTomb) continue;
+    const uint32_t id = low - 1u;
+    if (id >= live_end) continue;
+    unsigned long long pos = homes[id] & new_mask;
+    unsigned long long it = 0;
+    for (; it <= new_mask; ++it, pos = (pos + 1) & new_mask)
+      if (atomicCAS(new_t + pos, 0ull, v) == 0ull) break;
+    if (it > new_mask) {
+      atomicExch(error, 4u);
+      continue;
+    }
+    slotpos[id] = unsigned(pos);
   }
 }
 
@@ -1578,6 +1682,16 @@ cudaError_t Kernels<W>::batch_fixup(const StepProblem* steps, const uint4* moves
     k_batch_fixup<<<blocks, 256, 0, lc.stream>>>(steps, moves, n, dense_end, n_problems);
   }
   k_batch_set_entries<<<(std::max(n_problems, 1) + 255) / 256, 256, 0, lc.stream>>>(steps, dense_end, n_problems);
+  return cudaGetLastError();
+}
+
+template <typename W>
+cudaError_t Kernels<W>::rehash(const unsigned long long* old_t, unsigned long long old_cap, unsigned long long* new_t,
+                               unsigned long long new_cap, const unsigned* homes, unsigned* slotpos,
+                               unsigned live_end, unsigned* error, const LaunchCfg& lc) {
+  if (old_cap == 0) return cudaSuccess;
+  const unsigned blocks = unsigned(std::min<unsigned long long>((old_cap + 255) / 256, (unsigned long long)lc.sms * 8));
+  k_rehash<<<blocks, 256, 0, lc.stream>>>(old_t, old_cap, new_t, new_cap - 1, homes, slotpos, live_end, error);
   return cudaGetLastError();
 }
 

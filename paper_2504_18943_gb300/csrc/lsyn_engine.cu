@@ -1,0 +1,827 @@
+// Multi-problem scheduler: admission, cache growth, batch steps (see
+// lsyn_engine.h for the design).
+#include "lsyn_engine.h"
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+namespace lsyn {
+namespace {
+
+unsigned long long pow2_at_least(unsigned long long x) {
+  unsigned long long p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+unsigned long long pow2_at_most(unsigned long long x) {
+  unsigned long long p = 1;
+  while (p * 2 <= x) p <<= 1;
+  return x ? p : 0;
+}
+
+constexpr size_t kSmallBytes = 4u << 20;    // constants + atom rows: (5 + 32) * 64 KiB at most, rounded
+constexpr unsigned kDeferMin = 1u << 16, kDeferMax = 1u << 23;
+
+unsigned defer_cap_for(unsigned long long entries) {
+  return unsigned(std::max<unsigned long long>(kDeferMin, std::min<unsigned long long>(kDeferMax, entries / 16)));
+}
+
+}  // namespace
+
+Engine::~Engine() {
+  if (stream_) cudaStreamSynchronize(stream_);
+  for (auto& kv : graphs_) {
+    if (kv.second.second) cudaGraphExecDestroy(kv.second.second);
+    if (kv.second.first) cudaGraphDestroy(kv.second.first);
+  }
+  for (Slot& s : slots_) {
+    s.arena.release(pool_);
+    s.prov.release(pool_);
+    s.slotpos.release(pool_);
+    s.homes.release(pool_);
+    s.misc.release(pool_);
+    s.defer[0].release(pool_);
+    s.defer[1].release(pool_);
+    s.table[0].release(pool_);
+    s.table[1].release(pool_);
+  }
+  mem_.release_all();
+  if (h_ctrs_) cudaFreeHost(h_ctrs_);
+  if (h_hdr_) cudaFreeHost(h_hdr_);
+  if (h_steps_) cudaFreeHost(h_steps_);
+  if (h_dense_) cudaFreeHost(h_dense_);
+  if (h_stage_) cudaFreeHost(h_stage_);
+  if (h_fbuf_) cudaFreeHost(h_fbuf_);
+  if (h_fstatus_) cudaFreeHost(h_fstatus_);
+  if (own_stream_ && stream_) cudaStreamDestroy(stream_);
+}
+
+lsyn_status Engine::init(const lsyn_config* cfg, const lsyn_batch_tuning* tune, int max_active, bool keep_finished) {
+  memset(&cfg_, 0, sizeof(cfg_));
+  cfg_.device = -1;
+  if (cfg) cfg_ = *cfg;
+  if (!cfg_.cache_bytes) cfg_.cache_bytes = 1ull << 30;
+  memset(&tune_, 0, sizeof(tune_));
+  if (tune) tune_ = *tune;
+  if (tune_.blocks_per_sm < 1) tune_.blocks_per_sm = 4;
+  if (max_active < 1) { err = "max_active must be positive"; return LSYN_E_INVAL; }
+  tune_.max_active = max_active;
+  keep_finished_ = keep_finished;
+  cudaError_t e;
+  if (cfg_.device >= 0 && (e = cudaSetDevice(cfg_.device)) != cudaSuccess) { err = cudaGetErrorString(e); return LSYN_E_CUDA; }
+  if ((e = cudaGetDevice(&device_)) != cudaSuccess) { err = cudaGetErrorString(e); return LSYN_E_CUDA; }
+  if ((e = cudaDeviceGetAttribute(&sms_, cudaDevAttrMultiProcessorCount, device_)) != cudaSuccess) {
+    err = cudaGetErrorString(e);
+    return LSYN_E_CUDA;
+  }
+  stream_ = static_cast<cudaStream_t>(cfg_.stream);
+  if (!stream_) {  // the legacy default stream cannot be captured into a graph
+    if ((e = cudaStreamCreateWithFlags(&stream_, cudaStreamNonBlocking)) != cudaSuccess) {
+      err = cudaGetErrorString(e);
+      return LSYN_E_CUDA;
+    }
+    own_stream_ = true;
+  }
+  cfg_.stream = stream_;
+  size_t free_b = 0, total_b = 0;
+  if ((e = cudaMemGetInfo(&free_b, &total_b)) != cudaSuccess) { err = cudaGetErrorString(e); return LSYN_E_CUDA; }
+  size_t budget = tune_.pool_bytes ? size_t(tune_.pool_bytes) : size_t(double(free_b) * 0.9);
+  if (!pool_.init(device_, budget, &err)) return LSYN_E_CUDA;
+  tune_.pool_bytes = pool_.budget();
+
+  const int n = max_active;
+  const int cap_steps = int(pow2_at_least((unsigned long long)n));
+  slots_.resize(size_t(n));
+  mem_.alloc = cfg_.alloc;
+  mem_.free = cfg_.free;
+  mem_.user = cfg_.alloc_user;
+  ctrs_ = static_cast<DevCounters*>(mem_.get(sizeof(DevCounters) * size_t(n)));
+  holes_ = static_cast<uint2*>(mem_.get(sizeof(uint2) * size_t(hole_cap_) * size_t(n)));
+  d_hdr_ = static_cast<StepHeader*>(mem_.get(sizeof(StepHeader)));
+  d_steps_ = static_cast<StepProblem*>(mem_.get(sizeof(StepProblem) * size_t(cap_steps)));
+  d_moves_ = static_cast<uint4*>(mem_.get(sizeof(uint4) * size_t(move_cap_)));
+  d_dense_ = static_cast<unsigned*>(mem_.get(sizeof(unsigned) * size_t(n)));
+  fbuf_ = static_cast<char*>(mem_.get(lsyn_ctx::kFormulaCap));
+  fstatus_ = static_cast<int*>(mem_.get(sizeof(int)));
+  if (!ctrs_ || !holes_ || !d_hdr_ || !d_steps_ || !d_moves_ || !d_dense_ || !fbuf_ || !fstatus_) {
+    err = "device allocation failed";
+    return LSYN_E_NOMEM;
+  }
+  if (cudaMallocHost(&h_ctrs_, sizeof(DevCounters) * size_t(n)) != cudaSuccess ||
+      cudaMallocHost(&h_hdr_, sizeof(StepHeader)) != cudaSuccess ||
+      cudaMallocHost(&h_steps_, sizeof(StepProblem) * size_t(cap_steps)) != cudaSuccess ||
+      cudaMallocHost(&h_dense_, sizeof(unsigned) * size_t(n)) != cudaSuccess ||
+      cudaMallocHost(&h_stage_, sizeof(unsigned) * size_t(n)) != cudaSuccess ||
+      cudaMallocHost(&h_fbuf_, lsyn_ctx::kFormulaCap) != cudaSuccess ||
+      cudaMallocHost(&h_fstatus_, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    err = "pinned host allocation failed";
+    return LSYN_E_NOMEM;
+  }
+  memset(h_steps_, 0, sizeof(StepProblem) * size_t(cap_steps));
+  if ((e = cudaMemsetAsync(ctrs_, 0, sizeof(DevCounters) * size_t(n), stream_)) != cudaSuccess ||
+      (e = cudaMemsetAsync(d_steps_, 0, sizeof(StepProblem) * size_t(cap_steps), stream_)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(stream_)) != cudaSuccess) {
+    err = cudaGetErrorString(e);
+    return LSYN_E_CUDA;
+  }
+  return LSYN_OK;
+}
+
+void Engine::set_tune(const lsyn_batch_tuning& t) {
+  tune_.blocks_per_sm = t.blocks_per_sm > 0 ? t.blocks_per_sm : 4;
+  tune_.use_graph = t.use_graph;
+  tune_.predict_pct = t.predict_pct;
+  tune_.solo_candidates = t.solo_candidates;
+  if (stream_) cudaStreamSynchronize(stream_);
+  for (auto& kv : graphs_) {  // the launch shape is part of each graph
+    if (kv.second.second) cudaGraphExecDestroy(kv.second.second);
+    if (kv.second.first) cudaGraphDestroy(kv.second.first);
+  }
+  graphs_.clear();
+}
+
+lsyn_status Engine::make_job(const lsyn_problem* p, int max_size, Job* j) {
+  // The constants and atom rows are packed once; they are all a (re)admission needs.
+  j->max_size = max_size;
+  lsyn_config cfg = cfg_;
+  cfg.device = -1;  // may run on a caller's thread: leave its current device alone
+  lsyn_status s = ctx_shell(p, &cfg, false, &j->c, &j->consts, &j->atoms);
+  if (s != LSYN_OK) {
+    j->err = thread_error();
+    return s;
+  }
+  j->c->device = device_;
+  j->c->sms = sms_;
+
+  j->c->borrowed = true;
+  j->c->owns_host = false;
+  j->c->stream = stream_;
+  j->cap_entries = j->c->max_entries;
+  j->c->max_entries = 0;
+  j->c->table_cap = 0;
+  return LSYN_OK;
+}
+
+void Engine::enqueue(Job* j, double t_submit) {
+  j->t_submit = t_submit;
+  j->state = Job::kQueued;
+  j->status = LSYN_PENDING;
+  queue_.push_back(j);
+}
+
+// Address space for this job's largest cache (a slot keeps the largest
+// reservation any of its jobs needed).
+bool Engine::reserve_slot(Slot& s, const Job* j, std::string* e) {
+  const unsigned long long cap = j->cap_entries + 64;
+  const size_t M = size_t(j->c->vecs) * 16;
+  const double load = j->c->table_load;
+  const unsigned long long max_t =
+      std::max(pow2_at_least((unsigned long long)(double(cap) / load) + 2), (unsigned long long)(pool_.granularity() / 8));
+  auto fit = [&](Segment& sg, size_t bytes) {
+    if (sg.reserved() && sg.reserved() >= bytes + bytes / 2) return true;
+    sg.release(pool_);
+    return sg.reserve(pool_, bytes, e);
+  };
+  if (!fit(s.arena, size_t(cap) * M) || !fit(s.prov, size_t(cap) * 8) || !fit(s.slotpos, size_t(cap) * 4) ||
+      !fit(s.homes, size_t(cap) * 4) || !fit(s.misc, kSmallBytes) || !fit(s.defer[0], size_t(kDeferMax) * 8) ||
+      !fit(s.defer[1], size_t(kDeferMax) * 8) || !fit(s.table[0], size_t(max_t) * 8) ||
+      !fit(s.table[1], size_t(max_t) * 8))
+    return false;
+  s.reserved = true;
+  return true;
+}
+
+// Keep a small warm mapping for the slot's next job (all = drop everything).
+void Engine::trim_slot(Slot& s, bool all) {
+  cudaStreamSynchronize(stream_);  // nothing in flight may touch what is unmapped
+  const size_t g = all ? 0 : pool_.granularity();
+  s.arena.shrink(pool_, 2 * g);
+  s.prov.shrink(pool_, g);
+  s.slotpos.shrink(pool_, g);
+  s.homes.shrink(pool_, g);
+  s.misc.shrink(pool_, g);
+  s.defer[0].shrink(pool_, g);
+  s.defer[1].shrink(pool_, g);
+  s.table[s.cur_table].shrink(pool_, g);
+  s.table[1 - s.cur_table].shrink(pool_, 0);
+  s.tcap = 0;
+}
+
+lsyn_status Engine::bind(Job* j, int slot) {
+  Slot& s = slots_[size_t(slot)];
+  if (!reserve_slot(s, j, &err)) return LSYN_E_CUDA;
+  lsyn_ctx* c = j->c;
+  const size_t M = size_t(c->vecs) * 16;
+  const size_t small = (5 + size_t(c->n_props)) * M;
+  if (!s.misc.grow(pool_, small, &err)) return LSYN_E_NOMEM;
+  s.job = j;
+  s.tcap = 0;
+  j->slot = slot;
+  c->arena = static_cast<uint4*>(s.arena.ptr());
+  c->prov = static_cast<unsigned long long*>(s.prov.ptr());
+  c->slotpos = static_cast<unsigned*>(s.slotpos.ptr());
+  c->homes = static_cast<unsigned*>(s.homes.ptr());
+  c->consts = static_cast<uint4*>(s.misc.ptr());
+  c->atoms = c->consts + size_t(5) * c->vecs;
+  c->defer[0] = static_cast<unsigned long long*>(s.defer[0].ptr());
+  c->defer[1] = static_cast<unsigned long long*>(s.defer[1].ptr());
+  c->table = static_cast<unsigned long long*>(s.table[s.cur_table].ptr());
+  c->table_cap = 0;
+  c->max_entries = 0;
+  c->defer_cap = 0;
+  c->ctr = ctrs_ + slot;
+  c->holes = holes_ + size_t(slot) * hole_cap_;
+  c->hole_cap = hole_cap_;
+  c->fbuf = fbuf_;
+  c->fstatus = fstatus_;
+  c->h_fbuf = h_fbuf_;
+  c->h_fstatus = h_fstatus_;
+  c->level_start.assign(1, 0);
+  c->level_n.assign(1, 0);
+  c->levels_done = 0;
+  c->last_incomplete = false;
+  c->constructed = 0;
+  c->last_sol = ~0ull;
+  j->redo = false;
+  j->ratio = 1.0;
+  cudaError_t e = cudaMemcpyAsync(c->consts, j->consts.data(), j->consts.size() * 4, cudaMemcpyHostToDevice, stream_);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->atoms, j->atoms.data(), j->atoms.size() * 4, cudaMemcpyHostToDevice, stream_);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->ctr, 0, sizeof(DevCounters), stream_);
+  if (e != cudaSuccess) { err = cudaGetErrorString(e); return LSYN_E_CUDA; }
+  j->state = Job::kActive;
+  j->seq = next_seq_++;
+  j->t_admit = now_ms();
+  j->resident = true;
+  active_.push_back(j);
+  note_peak();
+  return LSYN_OK;
+}
+
+void Engine::unbind(Job* j, bool keep_cache) {
+  if (j->slot < 0) return;
+  if (keep_cache) return;
+  Slot& s = slots_[size_t(j->slot)];
+  trim_slot(s, false);
+  s.job = nullptr;
+  j->slot = -1;
+  j->resident = false;
+  lsyn_ctx* c = j->c;
+  c->levels_done = 0;  // read-only calls on the handle now see no levels
+  c->level_start.assign(1, 0);
+  c->level_n.assign(1, 0);
+  c->arena = nullptr;
+  c->prov = nullptr;
+  c->table = nullptr;
+  c->max_entries = 0;
+  c->table_cap = 0;
+}
+
+void Engine::release_job(Job* j) {
+  if (j->state == Job::kDone) unbind(j, false);
+}
+
+void Engine::evict(Job* j) {
+  active_.erase(std::remove(active_.begin(), active_.end(), j), active_.end());
+  unbind(j, false);
+  j->state = Job::kQueued;
+  j->redo = false;
+  ++j->evictions;
+  ++evictions_;
+  queue_.push_front(j);
+}
+
+void Engine::finish(Job* j, lsyn_status st) {
+  lsyn_ctx* c = j->c;
+  j->status = st;
+  j->t_done = now_ms();
+  j->levels_done = c->levels_done;
+  j->constructed = int64_t(c->constructed);
+  j->unique = int64_t(c->level_start.back() + c->level_n.back());
+  j->state = Job::kDone;
+  active_.erase(std::remove(active_.begin(), active_.end(), j), active_.end());
+  done_.push_back(j);
+  unbind(j, keep_finished_);
+}
+
+std::vector<Job*> Engine::take_done() {
+  std::vector<Job*> out;
+  out.swap(done_);
+  return out;
+}
+
+void Engine::clear() {
+  if (stream_) cudaStreamSynchronize(stream_);
+  for (Job* j : active_) {
+    unbind(j, false);
+    j->state = Job::kDone;
+  }
+  active_.clear();
+  queue_.clear();
+  for (Slot& s : slots_)
+    if (s.job) unbind(s.job, false);
+  done_.clear();
+}
+
+unsigned long long Engine::predict_entries(const Job* j, int k, unsigned long long cand) const {
+  const lsyn_ctx* c = j->c;
+  const unsigned long long start = c->level_start.back() + c->level_n.back();
+  unsigned long long add = cand;
+  if (k >= 3 && !j->redo) {
+    const double margin = (tune_.predict_pct > 0 ? tune_.predict_pct : 150) / 100.0;
+    const double r = std::min(1.0, margin * j->ratio);
+    add = std::min<unsigned long long>(cand, (unsigned long long)(double(cand) * r) + (tune_.predict_pct > 0 ? 1ull : 1024ull));
+  }
+  return std::min<unsigned long long>(j->cap_entries, start + add + 1);
+}
+
+size_t Engine::growth_cost(const Job* j, unsigned long long entries) const {
+  const Slot& s = slots_[size_t(j->slot)];
+  const lsyn_ctx* c = j->c;
+  const size_t M = size_t(c->vecs) * 16;
+  entries = std::min<unsigned long long>(entries, j->cap_entries);
+  size_t cost = 0;
+  auto add = [&](size_t x) { cost = (x == ~size_t(0) || cost == ~size_t(0)) ? ~size_t(0) : cost + x; };
+  const size_t cap = size_t(j->cap_entries);
+  add(s.arena.grow_cost(pool_, size_t(entries) * M, cap * M));
+  add(s.prov.grow_cost(pool_, size_t(entries) * 8, cap * 8));
+  add(s.slotpos.grow_cost(pool_, size_t(entries) * 4, cap * 4));
+  add(s.homes.grow_cost(pool_, size_t(entries) * 4, cap * 4));
+  const size_t dbytes = size_t(defer_cap_for(entries)) * 8;
+  const size_t dlimit = size_t(defer_cap_for(cap)) * 8;
+  add(s.defer[0].grow_cost(pool_, dbytes, dlimit));
+  add(s.defer[1].grow_cost(pool_, dbytes, dlimit));
+  const unsigned long long want_t = pow2_at_least((unsigned long long)(double(entries) / c->table_load) + 1);
+  if (want_t > s.tcap || j->redo) {
+    const size_t tb = size_t(std::max(want_t, s.tcap)) * 8;
+    add(s.tcap == 0 ? s.table[s.cur_table].grow_cost(pool_, tb) : s.table[1 - s.cur_table].grow_cost(pool_, tb));
+  }
+  return cost;
+}
+
+lsyn_status Engine::rebuild_table(Job* j, unsigned long long tcap, uint32_t live_end) {
+  Slot& s = slots_[size_t(j->slot)];
+  lsyn_ctx* c = j->c;
+  const LaunchCfg lc{stream_, sms_};
+  const bool fresh = s.tcap == 0;
+  Segment& dst = fresh ? s.table[s.cur_table] : s.table[1 - s.cur_table];
+  if (!dst.grow(pool_, size_t(tcap) * 8, &err)) return LSYN_E_NOMEM;
+  // use the whole mapping: a larger table costs only its clearing
+  tcap = std::max(tcap, pow2_at_most(dst.mapped() / 8));
+  auto* nt = static_cast<unsigned long long*>(dst.ptr());
+  cudaError_t e = cudaMemsetAsync(nt, 0, size_t(tcap) * 8, stream_);
+  if (e == cudaSuccess && !fresh) {
+    auto* ot = static_cast<unsigned long long*>(s.table[s.cur_table].ptr());
+    e = c->word_bits == 32
+            ? Kernels<uint32_t>::rehash(ot, s.tcap, nt, tcap, c->homes, c->slotpos, live_end, &c->ctr->error, lc)
+            : Kernels<uint64_t>::rehash(ot, s.tcap, nt, tcap, c->homes, c->slotpos, live_end, &c->ctr->error, lc);
+  }
+  if (e != cudaSuccess) { err = std::string("table rebuild: ") + cudaGetErrorString(e); return LSYN_E_CUDA; }
+  if (!fresh) {
+    trim_after_sync_.push_back(&s.table[s.cur_table]);
+    s.cur_table = 1 - s.cur_table;
+  }
+  s.tcap = tcap;
+  c->table = nt;
+  c->table_cap = tcap;
+  return LSYN_OK;
+}
+
+lsyn_status Engine::grow(Job* j, unsigned long long entries, bool* ok) {
+  *ok = false;
+  Slot& s = slots_[size_t(j->slot)];
+  lsyn_ctx* c = j->c;
+  const size_t M = size_t(c->vecs) * 16;
+  entries = std::max<unsigned long long>(1, std::min<unsigned long long>(entries, j->cap_entries));
+  const size_t cost = growth_cost(j, entries);
+  if (cost == ~size_t(0) || cost > pool_.available()) return LSYN_OK;
+  std::string e2;
+  const size_t cap = size_t(j->cap_entries);
+  const size_t dbytes = size_t(defer_cap_for(entries)) * 8;
+  const size_t dlimit = size_t(defer_cap_for(cap)) * 8;
+  if (!s.arena.grow(pool_, size_t(entries) * M, &e2, cap * M) ||
+      !s.prov.grow(pool_, size_t(entries) * 8, &e2, cap * 8) ||
+      !s.slotpos.grow(pool_, size_t(entries) * 4, &e2, cap * 4) ||
+      !s.homes.grow(pool_, size_t(entries) * 4, &e2, cap * 4) || !s.defer[0].grow(pool_, dbytes, &e2, dlimit) ||
+      !s.defer[1].grow(pool_, dbytes, &e2, dlimit))
+    return LSYN_OK;  // the pool ran short (another size class was needed): try again later
+  const unsigned long long live = c->level_start.back() + c->level_n.back();
+  const unsigned long long want_t = pow2_at_least((unsigned long long)(double(entries) / c->table_load) + 1);
+  if (want_t > s.tcap || j->redo) {
+    lsyn_status st = rebuild_table(j, std::max(want_t, s.tcap), uint32_t(live));
+    if (st == LSYN_E_NOMEM) return LSYN_OK;
+    if (st != LSYN_OK) return st;
+  }
+  if (j->redo) {
+    // the undone level's entries are gone from the table; the arena restarts at its first id
+    h_stage_[j->slot] = uint32_t(live);
+    cudaError_t e = cudaMemcpyAsync(&c->ctr->n_entries, &h_stage_[j->slot], sizeof(unsigned), cudaMemcpyHostToDevice,
+                                    stream_);
+    if (e != cudaSuccess) { err = cudaGetErrorString(e); return LSYN_E_CUDA; }
+  }
+  unsigned long long have = j->cap_entries;
+  have = std::min<unsigned long long>(have, s.arena.mapped() / M);
+  have = std::min<unsigned long long>(have, s.prov.mapped() / 8);
+  have = std::min<unsigned long long>(have, s.slotpos.mapped() / 4);
+  have = std::min<unsigned long long>(have, s.homes.mapped() / 4);
+  have = std::min<unsigned long long>(have, (unsigned long long)(double(s.tcap) * c->table_load));
+  c->max_entries = unsigned(have);
+  c->defer_cap = unsigned(std::min<size_t>(kDeferMax, std::min(s.defer[0].mapped(), s.defer[1].mapped()) / 8));
+  note_peak();
+  *ok = true;
+  return LSYN_OK;
+}
+
+lsyn_status Engine::admit() {
+  if (queue_.empty()) return LSYN_OK;
+  // memory the admitted jobs are predicted to need for their next level
+  size_t reserve = 0;
+  for (Job* j : active_) {
+    const int k = j->c->levels_done + 1;
+    const unsigned long long cand = (unsigned long long)std::max<int64_t>(0, level_candidate_count(j->c, k));
+    const size_t g = growth_cost(j, predict_entries(j, k, cand));
+    reserve += g == ~size_t(0) ? 0 : g;
+  }
+  size_t next_free = 0;
+  while (!queue_.empty()) {
+    while (next_free < slots_.size() && slots_[next_free].job) ++next_free;
+    if (next_free >= slots_.size()) {
+      // every slot is taken: free one kept only for a finished job's export
+      for (size_t i = 0; i < slots_.size(); ++i)
+        if (slots_[i].job && slots_[i].job->state == Job::kDone) {
+          unbind(slots_[i].job, false);
+          next_free = i;
+          break;
+        }
+      if (next_free >= slots_.size()) break;
+    }
+    Job* j = queue_.front();
+    // first levels: constants, warm arrays and a table (a few blocks)
+    const size_t M = size_t(j->c->vecs) * 16;
+    const size_t first = (5 + size_t(j->c->n_props)) * M + 16 * pool_.granularity();
+    if (!active_.empty() && pool_.available() < reserve + first) break;
+    queue_.pop_front();
+    lsyn_status s = bind(j, int(next_free));
+    if (s != LSYN_OK) {
+      slots_[next_free].job = nullptr;
+      j->slot = -1;
+      active_.erase(std::remove(active_.begin(), active_.end(), j), active_.end());
+      if (s != LSYN_E_NOMEM) return s;
+      if (!active_.empty()) {  // wait for memory
+        j->state = Job::kQueued;
+        queue_.push_front(j);
+        err.clear();
+        break;
+      }
+      // alone, it still does not fit: answer it
+      j->err = "the memory pool cannot hold this problem's constants";
+      j->status = LSYN_E_NOMEM;
+      j->state = Job::kDone;
+      j->t_done = now_ms();
+      done_.push_back(j);
+      err.clear();
+      continue;
+    }
+    reserve += first;
+  }
+  return LSYN_OK;
+}
+
+lsyn_status Engine::step() {
+  cudaSetDevice(device_);
+  std::sort(active_.begin(), active_.end(), [](const Job* a, const Job* b) { return a->seq < b->seq; });
+  std::vector<Job*> runnable, paused;
+  const std::vector<Job*> order = active_;
+  for (Job* j : order) {
+    const int k = j->c->levels_done + 1;
+    if (k > j->max_size) {
+      finish(j, LSYN_NOT_FOUND);
+      continue;
+    }
+    const unsigned long long cand = (unsigned long long)std::max<int64_t>(0, level_candidate_count(j->c, k));
+    bool ok = false;
+    lsyn_status s = grow(j, predict_entries(j, k, cand), &ok);
+    if (s != LSYN_OK) return s;
+    (ok ? runnable : paused).push_back(j);
+  }
+  if (runnable.empty() && !paused.empty()) {
+    // Nothing fits: free finished caches, then evict the youngest admitted jobs
+    // until the oldest can grow; alone, the oldest is capped at what it has.
+    Job* oldest = paused.front();
+    auto retry = [&]() -> bool {
+      const int k = oldest->c->levels_done + 1;
+      const unsigned long long cand = (unsigned long long)std::max<int64_t>(0, level_candidate_count(oldest->c, k));
+      bool ok = false;
+      if (grow(oldest, predict_entries(oldest, k, cand), &ok) != LSYN_OK) return false;
+      return ok;
+    };
+    bool ok = false;
+    for (Slot& s : slots_)
+      if (s.job && s.job->state == Job::kDone) unbind(s.job, false);
+    ok = retry();
+    while (!ok && active_.size() > 1) {
+      Job* young = *std::max_element(active_.begin(), active_.end(),
+                                     [](const Job* a, const Job* b) { return a->seq < b->seq; });
+      if (young == oldest) break;
+      evict(young);
+      ok = retry();
+    }
+    if (!ok) {
+      lsyn_ctx* c = oldest->c;
+      const unsigned long long live = c->level_start.back() + c->level_n.back();
+      if (c->max_entries >= live && slots_[size_t(oldest->slot)].tcap > 0 && !oldest->redo) {
+        oldest->capped = true;
+        oldest->cap_entries = c->max_entries;
+        oldest->err = "the memory pool could not hold this cache: capped at " + std::to_string(c->max_entries) +
+                      " entries";
+        ok = true;
+      } else {
+        oldest->err = "the memory pool cannot hold this problem's next level";
+        finish(oldest, LSYN_E_NOMEM);
+      }
+    }
+    if (ok) runnable.push_back(oldest);
+  }
+  // one batch launch per word size
+  for (int wb : {64, 32}) {
+    std::vector<Plan> g;
+    for (Job* j : runnable)
+      if (j->state == Job::kActive && j->c->word_bits == wb) g.push_back(Plan{j, j->c->levels_done + 1, LevelPlan()});
+    if (g.empty()) continue;
+    lsyn_status s = run_group(g, wb);
+    if (s != LSYN_OK) return s;
+  }
+  cudaError_t e = cudaStreamSynchronize(stream_);
+  if (e != cudaSuccess) { err = std::string("step sync: ") + cudaGetErrorString(e); return LSYN_E_CUDA; }
+  for (Segment* sg : trim_after_sync_) {
+    bool current = false;
+    for (Slot& s : slots_)
+      if (&s.table[s.cur_table] == sg) current = true;
+    if (!current) sg->shrink(pool_, 0);
+  }
+  trim_after_sync_.clear();
+  ++steps_;
+  return LSYN_OK;
+}
+
+lsyn_status Engine::launch_step(int word_bits, int n, const std::vector<Plan>& g) {
+  LaunchCfg lc{stream_, sms_};
+  cudaError_t e;
+  if (tune_.use_graph) {
+    const int bucket = int(pow2_at_least((unsigned long long)n));
+    auto& gr = graphs_[{word_bits, bucket}];
+    if (!gr.second) {
+      e = cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) { err = std::string("graph capture: ") + cudaGetErrorString(e); return LSYN_E_CUDA; }
+      cudaMemcpyAsync(d_hdr_, h_hdr_, sizeof(StepHeader), cudaMemcpyHostToDevice, stream_);
+      cudaMemcpyAsync(d_steps_, h_steps_, sizeof(StepProblem) * size_t(bucket), cudaMemcpyHostToDevice, stream_);
+      if (word_bits == 32) {
+        Kernels<uint32_t>::batch_begin(d_hdr_, d_steps_, bucket, lc);
+        Kernels<uint32_t>::batch_run(d_hdr_, d_steps_, lc, tune_.blocks_per_sm);
+      } else {
+        Kernels<uint64_t>::batch_begin(d_hdr_, d_steps_, bucket, lc);
+        Kernels<uint64_t>::batch_run(d_hdr_, d_steps_, lc, tune_.blocks_per_sm);
+      }
+      e = cudaStreamEndCapture(stream_, &gr.first);
+      if (e != cudaSuccess) { err = std::string("graph capture: ") + cudaGetErrorString(e); return LSYN_E_CUDA; }
+      e = cudaGraphInstantiate(&gr.second, gr.first, 0);
+      if (e != cudaSuccess) { err = std::string("graph instantiate: ") + cudaGetErrorString(e); return LSYN_E_CUDA; }
+    }
+    e = cudaGraphLaunch(gr.second, stream_);
+    if (e != cudaSuccess) { err = std::string("graph launch: ") + cudaGetErrorString(e); return LSYN_E_CUDA; }
+  } else {
+    e = cudaMemcpyAsync(d_hdr_, h_hdr_, sizeof(StepHeader), cudaMemcpyHostToDevice, stream_);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_steps_, h_steps_, sizeof(StepProblem) * size_t(n), cudaMemcpyHostToDevice, stream_);
+    if (e == cudaSuccess)
+      e = word_bits == 32 ? Kernels<uint32_t>::batch_begin(d_hdr_, d_steps_, n, lc)
+                          : Kernels<uint64_t>::batch_begin(d_hdr_, d_steps_, n, lc);
+    if (e == cudaSuccess)
+      e = word_bits == 32 ? Kernels<uint32_t>::batch_run(d_hdr_, d_steps_, lc, tune_.blocks_per_sm)
+                          : Kernels<uint64_t>::batch_run(d_hdr_, d_steps_, lc, tune_.blocks_per_sm);
+    if (e != cudaSuccess) { err = std::string("batch step: ") + cudaGetErrorString(e); return LSYN_E_CUDA; }
+  }
+  // Levels large enough to fill the GPU alone run with the one-problem kernels
+  // (their counters were reset with the step's).
+  for (size_t i = 0; i < g.size(); ++i) {
+    const Plan& p = g[i];
+    if (!p.solo) continue;
+    const CacheView& cv = h_steps_[i].cv;
+    if (p.lp.uops && p.lp.u_count) {
+      e = word_bits == 32 ? Kernels<uint32_t>::unary(cv, p.lp.u_first, p.lp.u_count, p.lp.uops, lc)
+                          : Kernels<uint64_t>::unary(cv, p.lp.u_first, p.lp.u_count, p.lp.uops, lc);
+      if (e != cudaSuccess) { err = std::string("unary kernel: ") + cudaGetErrorString(e); return LSYN_E_CUDA; }
+    }
+    if (p.lp.plan.n_splits > 0) {
+      e = word_bits == 32 ? Kernels<uint32_t>::binary(cv, p.lp.plan, lc) : Kernels<uint64_t>::binary(cv, p.lp.plan, lc);
+      if (e != cudaSuccess) { err = std::string("binary kernel: ") + cudaGetErrorString(e); return LSYN_E_CUDA; }
+    }
+  }
+  e = cudaMemcpyAsync(h_ctrs_, ctrs_, sizeof(DevCounters) * slots_.size(), cudaMemcpyDeviceToHost, stream_);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream_);
+  if (e != cudaSuccess) { err = std::string("batch step sync: ") + cudaGetErrorString(e); return LSYN_E_CUDA; }
+  return LSYN_OK;
+}
+
+// Deferred-only passes reuse the step arrays without the counter reset.
+lsyn_status Engine::launch_plain(int word_bits, int n) {
+  LaunchCfg lc{stream_, sms_};
+  cudaError_t e = cudaMemcpyAsync(d_hdr_, h_hdr_, sizeof(StepHeader), cudaMemcpyHostToDevice, stream_);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_steps_, h_steps_, sizeof(StepProblem) * size_t(n), cudaMemcpyHostToDevice, stream_);
+  if (e == cudaSuccess)
+    e = word_bits == 32 ? Kernels<uint32_t>::batch_run(d_hdr_, d_steps_, lc, tune_.blocks_per_sm)
+                        : Kernels<uint64_t>::batch_run(d_hdr_, d_steps_, lc, tune_.blocks_per_sm);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h_ctrs_, ctrs_, sizeof(DevCounters) * slots_.size(), cudaMemcpyDeviceToHost, stream_);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream_);
+  if (e != cudaSuccess) { err = std::string("batch pass: ") + cudaGetErrorString(e); return LSYN_E_CUDA; }
+  return LSYN_OK;
+}
+
+lsyn_status Engine::run_group(std::vector<Plan>& g, int word_bits) {
+  const int n = int(g.size());
+  const unsigned long long warps = (unsigned long long)sms_ * unsigned(tune_.blocks_per_sm) * 8ull;
+  // 1. plan every job's level and pack the step array
+  unsigned long long tu = 0, tb = 0, td = 0;
+  for (int i = 0; i < n; ++i) {
+    Plan& p = g[size_t(i)];
+    lsyn_ctx* c = p.j->c;
+    ctx_level_plan(c, p.k, &p.lp);
+    if (p.lp.plan.n_splits > kBatchSplits) {
+      err = "too many splits for a batch level";
+      return LSYN_E_UNSUPPORTED;
+    }
+    const unsigned long long cand = (unsigned long long)std::max<int64_t>(0, level_candidate_count(c, p.k));
+    const unsigned long long solo_min = tune_.solo_candidates ? tune_.solo_candidates : (1ull << 19);
+    p.solo = p.k >= 2 && cand > solo_min;
+    // In the persistent launch warps move between problems and return their
+    // unused ids at each move: size the id chunk by this job's expected
+    // inserts over the launch's warps. Solo levels keep the one-problem size.
+    if (!p.solo) c->chunk = unsigned(std::max(1ull, std::min<unsigned long long>(c->chunk, (cand + 32ull) / (8ull * warps))));
+    StepProblem& sp = h_steps_[i];
+    memset(&sp, 0, sizeof(sp));
+    sp.cv = c->view(c->defer[0], &c->ctr->defer_n[0]);
+    sp.d_items_begin = td;
+    sp.u_items_begin = tu;
+    sp.b_items_begin = tb;
+    if (p.solo) {
+      // no items: the counters are reset with the step, the work is launched after it
+    } else if (p.k == 1) {
+      sp.d_n = unsigned(c->n_props);
+      sp.d_list = nullptr;
+      td += (sp.d_n + 31u) / 32u;
+    } else {
+      sp.u_first = p.lp.u_first;
+      sp.u_count = p.lp.u_count;
+      sp.u_ops = p.lp.uops;
+      tu += (sp.u_count + 7u) / 8u;
+      sp.b_ops = p.lp.plan.ops;
+      sp.n_splits = uint32_t(p.lp.plan.n_splits);
+      for (int t = 0; t < p.lp.plan.n_splits; ++t) sp.s[t] = p.lp.plan.s[t];
+      tb += (p.lp.plan.total_pairs + 7ull) / 8ull;
+    }
+  }
+  memset(h_hdr_, 0, sizeof(StepHeader));
+  h_hdr_->total_u = tu;
+  h_hdr_->total_b = tb;
+  h_hdr_->total_d = td;
+  h_hdr_->n = n;
+  lsyn_status s = launch_step(word_bits, n, g);
+  if (s != LSYN_OK) return s;
+
+  // 2. deferred candidates of every job, one launch per pass
+  for (int pass = 0;; ++pass) {
+    std::vector<int> need;
+    for (int i = 0; i < n; ++i) {
+      const Plan& p = g[size_t(i)];
+      const DevCounters& h = h_ctrs_[p.j->slot];
+      if (h.defer_overflow) { err = "deferred list overflow"; return LSYN_E_STATE; }
+      if (h.error) { err = "consistency check " + std::to_string(h.error) + " failed"; return LSYN_E_STATE; }
+      if (std::min(h.defer_n[p.cur], p.j->c->defer_cap)) need.push_back(i);
+    }
+    if (need.empty()) break;
+    if (pass >= 48) { err = "deferred candidates did not settle"; return LSYN_E_STATE; }
+    unsigned long long td2 = 0;
+    for (size_t q = 0; q < need.size(); ++q) {
+      Plan& p = g[size_t(need[q])];
+      lsyn_ctx* c = p.j->c;
+      const unsigned cnt = std::min(h_ctrs_[p.j->slot].defer_n[p.cur], c->defer_cap);
+      p.deferred += cnt;
+      cudaError_t e = cudaMemsetAsync(&c->ctr->defer_n[1 - p.cur], 0, sizeof(unsigned), stream_);
+      if (e != cudaSuccess) { err = cudaGetErrorString(e); return LSYN_E_CUDA; }
+      StepProblem& sp = h_steps_[q];
+      memset(&sp, 0, sizeof(sp));
+      sp.cv = c->view(c->defer[1 - p.cur], &c->ctr->defer_n[1 - p.cur]);
+      sp.cv.early_exit = 0;  // a deferred candidate must be settled even after a solution
+      sp.d_list = c->defer[p.cur];
+      sp.d_n = cnt;
+      sp.d_items_begin = td2;
+      td2 += (cnt + 31u) / 32u;
+      p.cur = 1 - p.cur;
+    }
+    memset(h_hdr_, 0, sizeof(StepHeader));
+    h_hdr_->total_d = td2;
+    h_hdr_->n = int(need.size());
+    if ((s = launch_plain(word_bits, int(need.size()))) != LSYN_OK) return s;
+  }
+
+  // 3. levels that outgrew the prediction are undone (unless a solution settles them)
+  for (Plan& p : g) {
+    lsyn_ctx* c = p.j->c;
+    const DevCounters& h = h_ctrs_[p.j->slot];
+    p.undo = h.full && c->max_entries < p.j->cap_entries && (!h.solved || c->full_levels);
+    p.total = std::min(h.n_entries, c->max_entries);
+  }
+
+  // 4. hole fixups of the kept levels: copy the hole logs, plan, one launch
+  std::vector<std::vector<uint2>> logs(static_cast<size_t>(n));
+  bool any_holes = false;
+  for (int i = 0; i < n; ++i) {
+    const Plan& p = g[size_t(i)];
+    const DevCounters& h = h_ctrs_[p.j->slot];
+    if (p.undo || !h.holes_n) continue;
+    if (h.holes_n > hole_cap_) { err = "hole log overflow"; return LSYN_E_STATE; }
+    logs[size_t(i)].resize(h.holes_n);
+    cudaError_t e = cudaMemcpyAsync(logs[size_t(i)].data(), p.j->c->holes, h.holes_n * sizeof(uint2),
+                                    cudaMemcpyDeviceToHost, stream_);
+    if (e != cudaSuccess) { err = cudaGetErrorString(e); return LSYN_E_CUDA; }
+    any_holes = true;
+  }
+  if (any_holes) {
+    cudaError_t e = cudaStreamSynchronize(stream_);
+    if (e != cudaSuccess) { err = std::string("hole log copy: ") + cudaGetErrorString(e); return LSYN_E_CUDA; }
+    std::vector<uint4> mv_all;
+    for (int i = 0; i < n; ++i) {
+      Plan& p = g[size_t(i)];
+      lsyn_ctx* c = p.j->c;
+      memset(&h_steps_[i], 0, sizeof(StepProblem));
+      h_steps_[i].cv = c->view(c->defer[0], &c->ctr->defer_n[0]);
+      h_dense_[i] = 0xFFFFFFFFu;
+      if (logs[size_t(i)].empty()) continue;
+      std::vector<uint2> mv;
+      const uint32_t dense = plan_hole_moves(logs[size_t(i)].data(), unsigned(logs[size_t(i)].size()), p.lp.start,
+                                             p.total, &mv);
+      for (const uint2& m : mv) mv_all.push_back(make_uint4(unsigned(i), m.x, m.y, 0));
+      p.total = dense;
+      h_dense_[i] = dense;
+    }
+    if (mv_all.size() > move_cap_) { err = "too many hole moves"; return LSYN_E_STATE; }
+    e = cudaMemcpyAsync(d_steps_, h_steps_, sizeof(StepProblem) * size_t(n), cudaMemcpyHostToDevice, stream_);
+    if (e == cudaSuccess && !mv_all.empty())
+      e = cudaMemcpyAsync(d_moves_, mv_all.data(), mv_all.size() * sizeof(uint4), cudaMemcpyHostToDevice, stream_);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_dense_, h_dense_, sizeof(unsigned) * size_t(n), cudaMemcpyHostToDevice, stream_);
+    LaunchCfg lc{stream_, sms_};
+    if (e == cudaSuccess)
+      e = word_bits == 32
+              ? Kernels<uint32_t>::batch_fixup(d_steps_, d_moves_, unsigned(mv_all.size()), d_dense_, n, lc)
+              : Kernels<uint64_t>::batch_fixup(d_steps_, d_moves_, unsigned(mv_all.size()), d_dense_, n, lc);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h_ctrs_, ctrs_, sizeof(DevCounters) * slots_.size(), cudaMemcpyDeviceToHost, stream_);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream_);
+    if (e != cudaSuccess) { err = std::string("batch fixup: ") + cudaGetErrorString(e); return LSYN_E_CUDA; }
+  }
+
+  // 5. commit, answer, or schedule the redo
+  for (Plan& p : g) {
+    Job* j = p.j;
+    lsyn_ctx* c = j->c;
+    const DevCounters h = h_ctrs_[j->slot];
+    if (p.undo) {
+      j->redo = true;
+      ++j->redos;
+      ++redos_;
+      continue;
+    }
+    if (h.error) { err = "hole fixup found an inconsistent slot"; return LSYN_E_STATE; }
+    lsyn_level_stats st;
+    s = ctx_commit_level(c, p.k, h, p.total, p.deferred, p.lp, &st);
+    if (s != LSYN_OK) { err = c->err; return s; }
+    j->redo = false;
+    if (st.candidates > 0 && !st.early_exit) j->ratio = double(st.unique) / double(st.candidates);
+    if (st.solved) {
+      std::vector<char> text(lsyn_ctx::kFormulaCap);
+      s = ctx_reconstruct(c, &c->ctr->sol, text.data(), text.size());
+      if (s != LSYN_OK) {
+        j->err = c->err;
+        finish(j, s);
+        continue;
+      }
+      j->formula = text.data();
+      j->found = 1;
+      j->size = p.k;
+      j->exact = 1;
+      finish(j, LSYN_OK);
+    } else if (st.cache_full) {
+      if (j->err.empty()) j->err = "language cache full at level " + std::to_string(p.k);
+      finish(j, LSYN_E_CACHE_FULL);
+    }
+  }
+  return LSYN_OK;
+}
+
+}  // namespace lsyn

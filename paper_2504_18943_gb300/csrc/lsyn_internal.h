@@ -73,6 +73,7 @@ struct CacheView {
   unsigned int* defer_out_n;
   unsigned int defer_cap;
   unsigned int* slotpos;         // [max_entries]: table slot of each entry (for hole fixup)
+  unsigned int* homes;           // [max_entries]: low 32 bits of each entry's hash (table rebuilds)
   uint2* holes;                  // [hole_cap]: unused id ranges [x, y) left by warps
   unsigned int hole_cap;
   unsigned int chunk;            // ids a warp reserves per counter update (path B)
@@ -153,6 +154,11 @@ struct Kernels {
   // Moves (problem index, src, dst) of a batch step; then each problem's entry count.
   static cudaError_t batch_fixup(const StepProblem* steps, const uint4* moves, unsigned n, const unsigned* dense_end,
                                  int n_problems, const LaunchCfg& lc);
+  // Rebuild a table into a cleared one (new_cap slots, a power of two) from
+  // the entries below live_end; error receives 4 if the new table overflows.
+  static cudaError_t rehash(const unsigned long long* old_t, unsigned long long old_cap, unsigned long long* new_t,
+                            unsigned long long new_cap, const unsigned* homes, unsigned* slotpos, unsigned live_end,
+                            unsigned* error, const LaunchCfg& lc);
   // Move entries src -> dst (pairs), repointing their table slots.
   static cudaError_t fixup(const CacheView& cv, const uint2* moves, unsigned n, const LaunchCfg& lc);
   // Evaluate a postorder node list on every trace word: scratch [n_nodes][words].

@@ -71,7 +71,27 @@ class lsyn_result(ctypes.Structure):
 
 
 class lsyn_batch_tuning(ctypes.Structure):
-    _fields_ = [("blocks_per_sm", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+    _fields_ = [("blocks_per_sm", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("max_active", ctypes.c_int32),
+                ("predict_pct", ctypes.c_int32), ("pool_bytes", ctypes.c_uint64),
+                ("solo_candidates", ctypes.c_uint64)]
+
+
+class lsyn_sched_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("active", ctypes.c_int64),
+                ("queued", ctypes.c_int64), ("steps", ctypes.c_int64), ("evictions", ctypes.c_int64),
+                ("redos", ctypes.c_int64), ("reserved0", ctypes.c_int64), ("pool_bytes", ctypes.c_uint64),
+                ("pool_in_use", ctypes.c_uint64), ("pool_peak", ctypes.c_uint64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
+
+
+def make_tuning(blocks_per_sm: int = 0, use_graph: int = 0, max_active: int = 0, pool_bytes: int = 0,
+                predict_pct: int = 0, solo_candidates: int = 0) -> lsyn_batch_tuning:
+    t = lsyn_batch_tuning()
+    t.blocks_per_sm, t.use_graph, t.max_active, t.pool_bytes = blocks_per_sm, use_graph, max_active, pool_bytes
+    t.predict_pct, t.solo_candidates = predict_pct, solo_candidates
+    return t
 
 
 class LsynError(RuntimeError):
@@ -124,6 +144,22 @@ def _load_library():
     lib.lsyn_batch_last_error.argtypes = [vp]
     lib.lsyn_batch_destroy.restype = None
     lib.lsyn_batch_destroy.argtypes = [vp]
+    lib.lsyn_batch_stats.restype = i32
+    lib.lsyn_batch_stats.argtypes = [vp, P(lsyn_sched_stats)]
+    lib.lsyn_server_create.restype = i32
+    lib.lsyn_server_create.argtypes = [P(lsyn_config), P(lsyn_batch_tuning), P(vp)]
+    lib.lsyn_submit.restype = i32
+    lib.lsyn_submit.argtypes = [vp, P(lsyn_problem), i32, P(ctypes.c_uint64)]
+    lib.lsyn_poll.restype = i32
+    lib.lsyn_poll.argtypes = [vp, ctypes.c_uint64, P(lsyn_result)]
+    lib.lsyn_wait.restype = i32
+    lib.lsyn_wait.argtypes = [vp, ctypes.c_uint64, i32, P(lsyn_result)]
+    lib.lsyn_server_stats.restype = i32
+    lib.lsyn_server_stats.argtypes = [vp, P(lsyn_sched_stats)]
+    lib.lsyn_server_last_error.restype = ctypes.c_char_p
+    lib.lsyn_server_last_error.argtypes = [vp]
+    lib.lsyn_server_destroy.restype = None
+    lib.lsyn_server_destroy.argtypes = [vp]
     return lib
 
 
@@ -466,6 +502,12 @@ def lsyn_batch_destroy(batch) -> None:
     _lib.lsyn_batch_destroy(batch)
 
 
+def lsyn_batch_stats(batch) -> dict:
+    st = lsyn_sched_stats()
+    _check(_lib.lsyn_batch_stats(batch, ctypes.byref(st)), None)
+    return st.as_dict()
+
+
 class Batch:
     """Owns a batch: ``with Batch(problems, cfg) as b: statuses, results, formulas = b.solve(13)``."""
 
@@ -504,3 +546,102 @@ class Batch:
     def export(self, i: int, k: int) -> np.ndarray:
         p = self.problems[i]
         return lsyn_export_level(lsyn_batch_problem(self.handle, i), k, p.n_traces, p.word_bits)
+
+    def stats(self) -> dict:
+        return lsyn_batch_stats(self.handle)
+
+
+# ---------------------------------------------------------------------------
+# Serving
+# ---------------------------------------------------------------------------
+
+def _server_err(sv) -> str:
+    m = _lib.lsyn_server_last_error(sv)
+    return m.decode() if m else ""
+
+
+def lsyn_server_create(config: Optional[lsyn_config] = None,
+                       tuning: Optional[lsyn_batch_tuning] = None) -> ctypes.c_void_p:
+    sv = ctypes.c_void_p()
+    st = _lib.lsyn_server_create(ctypes.byref(config) if config is not None else None,
+                                 ctypes.byref(tuning) if tuning is not None else None, ctypes.byref(sv))
+    if st != LSYN_OK:
+        raise LsynError(st, _server_err(None))
+    return sv
+
+
+def lsyn_submit(server, problem: PackedProblem, max_size: int) -> int:
+    t = ctypes.c_uint64()
+    st = _lib.lsyn_submit(server, ctypes.byref(problem.struct), max_size, ctypes.byref(t))
+    if st != LSYN_OK:
+        raise LsynError(st, _server_err(server))
+    return t.value
+
+
+def _answer(fn, server, ticket, *args, formula_cap: int = 4096):
+    r = lsyn_result()
+    buf = ctypes.create_string_buffer(formula_cap)
+    r.formula = ctypes.cast(buf, ctypes.c_char_p)
+    r.formula_cap = formula_cap
+    st = fn(server, ticket, *args, ctypes.byref(r))
+    if st == LSYN_E_INVAL:
+        raise LsynError(st, _server_err(server))
+    return st, r, (buf.value.decode() if st == LSYN_OK else None)
+
+
+def lsyn_poll(server, ticket: int):
+    """(status, result, formula); status LSYN_PENDING while the problem runs."""
+    return _answer(_lib.lsyn_poll, server, ticket)
+
+
+def lsyn_wait(server, ticket: int, timeout_ms: int = -1):
+    """(status, result, formula); LSYN_E_TIMEOUT if still pending after timeout_ms."""
+    return _answer(_lib.lsyn_wait, server, ticket, timeout_ms)
+
+
+def lsyn_server_stats(server) -> dict:
+    st = lsyn_sched_stats()
+    _check(_lib.lsyn_server_stats(server, ctypes.byref(st)), None)
+    return st.as_dict()
+
+
+def lsyn_server_destroy(server) -> None:
+    _lib.lsyn_server_destroy(server)
+
+
+class Server:
+    """Owns a server: ``with Server(cfg) as s: t = s.submit(p, 13); st, res, f = s.wait(t)``."""
+
+    def __init__(self, config: Optional[lsyn_config] = None, tuning: Optional[lsyn_batch_tuning] = None):
+        self.config = config
+        self.handle = lsyn_server_create(config, tuning)
+        self._keep = {}  # problems stay alive until answered (the library copies them anyway)
+
+    def close(self):
+        if self.handle:
+            lsyn_server_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def submit(self, problem: PackedProblem, max_size: int) -> int:
+        return lsyn_submit(self.handle, problem, max_size)
+
+    def poll(self, ticket: int):
+        return lsyn_poll(self.handle, ticket)
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        return lsyn_wait(self.handle, ticket, timeout_ms)
+
+    def stats(self) -> dict:
+        return lsyn_server_stats(self.handle)

@@ -28,7 +28,7 @@ def declared_functions():
 def test_header_declares_the_boundary():
     names = declared_functions()
     for required in ("lsyn_create", "lsyn_enumerate_level", "lsyn_solve", "lsyn_destroy", "lsyn_export_level",
-                     "lsyn_eval"):
+                     "lsyn_eval", "lsyn_submit", "lsyn_poll", "lsyn_batch_create", "lsyn_batch_solve"):
         assert required in names
 
 
@@ -116,3 +116,29 @@ def test_pack_traces_layout(L):
     p = L.pack_traces(bits, np.array([5, 3], dtype=np.int32), 1, 1, 32)
     assert p.atom_words.shape == (3, 2)
     assert p.atom_words[1, 0] == 0b10001 and p.atom_words[2, 1] == 0b100 and p.atom_words[0].sum() == 0
+
+
+def test_scheduler_entry_points_check_arguments_without_a_gpu(L):
+    lib = L._lib
+    r = L.lsyn_result()
+    assert lib.lsyn_poll(None, 1, ctypes.byref(r)) == L.LSYN_E_INVAL
+    assert lib.lsyn_wait(None, 1, 0, ctypes.byref(r)) == L.LSYN_E_INVAL
+    t = ctypes.c_uint64()
+    assert lib.lsyn_submit(None, None, 5, ctypes.byref(t)) == L.LSYN_E_INVAL
+    assert lib.lsyn_batch_solve(None, 5, None, None) == L.LSYN_E_INVAL
+    assert lib.lsyn_batch_stats(None, None) == L.LSYN_E_INVAL
+    assert lib.lsyn_server_stats(None, None) == L.LSYN_E_INVAL
+    out = ctypes.c_void_p()
+    assert lib.lsyn_batch_create(None, 0, None, None, ctypes.byref(out)) == L.LSYN_E_INVAL
+    assert L._batch_err(None)
+    lib.lsyn_batch_destroy(None)
+    lib.lsyn_server_destroy(None)
+
+
+def test_server_create_fails_cleanly_without_a_gpu(L):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(L.LsynError) as ei:
+        L.lsyn_server_create(L.make_config(cache_bytes=1 << 26))
+    assert ei.value.status < 0

@@ -78,11 +78,62 @@ def test_batch_graph_and_autotune(L, problems):
     assert t.blocks_per_sm in (2, 4, 6, 8) and t.use_graph in (0, 1)
 
 
-def test_batch_rejects_mixed_word_sizes(L, problems):
-    a = L.pack_problem(problems[0])
-    p = problems[1]
-    b32 = L.pack_traces(p.traces.bits, p.traces.lengths, p.n_pos, p.n_neg, 64)
-    b32 = L.PackedProblem(b32.n_props, b32.n_pos, b32.n_neg, 32, b32.lengths, b32.atom_words.astype(np.uint32))
-    with pytest.raises(L.LsynError) as ei:
-        L.Batch([a, b32])
-    assert ei.value.status == L.LSYN_E_INVAL
+def _plain(L, packed, cfg, max_size):
+    with L.Synthesizer(packed, cfg) as s:
+        st, res, f, _ = s.solve(max_size)
+        return st, res.size, res.unique
+
+
+def _assert_matches_plain(L, problems, packed, got, cfg_plain, max_size):
+    statuses, results, formulas = got
+    for i, p in enumerate(problems):
+        st, size, unique = _plain(L, packed[i], cfg_plain, max_size)
+        assert statuses[i] == st, (i, statuses[i], st)
+        if st == L.LSYN_OK:
+            assert results[i].size == size, (i, results[i].size, size)
+            spec = oracle.Spec.from_problem(p)
+            assert spec.separates(formulas[i]) and W.formula_size(formulas[i]) == size
+        elif st == L.LSYN_NOT_FOUND:
+            assert results[i].unique == unique, (i, results[i].unique, unique)
+
+
+def test_batch_mixed_word_sizes(L):
+    """32- and 64-bit problems in one batch (one launch per word size a step)."""
+    small = [W.mid_problem(s, oracle.labeller) for s in range(4)]
+    packed = [L.pack_traces(p.traces.bits, p.traces.lengths, p.n_pos, p.n_neg, 32 if n % 2 else 64)
+              for n, p in enumerate(small)]
+    cfg = L.make_config(cache_bytes=1 << 30)
+    with L.Batch(packed, cfg) as b:
+        got = b.solve(6)
+    _assert_matches_plain(L, small, packed, got, cfg, 6)
+
+
+def test_small_pool_evicts_and_caps_like_the_plain_path(L, problems):
+    """A pool of 1 GiB shared by 24 problems capped at 256 MiB each: problems
+    wait, are evicted and restarted, yet each answers as it does alone with a
+    256 MiB cache (cache-full ones included)."""
+    packed = [L.pack_problem(p) for p in problems]
+    cfg = L.make_config(cache_bytes=256 << 20)
+    with L.Batch(packed, cfg, L.make_tuning(pool_bytes=1 << 30)) as b:
+        got = b.solve(10)
+        stats = b.stats()
+    assert stats["pool_peak"] <= 1 << 30
+    _assert_matches_plain(L, problems, packed, got, cfg, 10)
+    assert any(s == L.LSYN_E_CACHE_FULL for s in got[0])
+
+
+def test_underpredicted_levels_are_redone(L, problems):
+    """With a 5% prediction margin most growing levels overflow their first
+    allocation; undone and re-run, they give the plain path's levels."""
+    packed = [L.pack_problem(p) for p in problems[:12]]
+    cfg = L.make_config(cache_bytes=1 << 30, full_levels=True)
+    with L.Batch(packed, cfg, L.make_tuning(predict_pct=5)) as b:
+        statuses, results, _ = b.solve(7)
+        stats = b.stats()
+        assert stats["redos"] > 0
+        for i in range(len(packed)):
+            with L.Synthesizer(packed[i], cfg) as s:
+                st, res, f, _ = s.solve(7)
+                assert statuses[i] == st
+                for k in _complete_levels(st, res):
+                    assert np.array_equal(canon(b.export(i, k)), canon(s.export(k))), (i, k)
