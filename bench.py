@@ -324,6 +324,190 @@ def run_lsyn(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# Batched and served workloads (problems/s, time-to-formula)
+# ---------------------------------------------------------------------------
+
+BATCH_N = 256
+BATCH_MAX_SIZE = 13
+BATCH_CACHE = 8 << 30  # each problem's cap: the same for the batch, the server and the plain path
+BATCH_WORKLOAD = ("batched: 256 seeded problems (base seed 1000) of the batched distribution: props U[2,8], "
+                  "traces U[8,512] split evenly, lengths U[8,64] (uint64 words), hidden size U[5,13]; "
+                  "max size 13, 8 GiB cache cap per problem")
+
+
+def _batched_problems(L, W, n=BATCH_N):
+    return [L.pack_problem(W.batched_problem(1000, i, L.labeller)) for i in range(n)]
+
+
+def _percentile(xs, q):
+    xs = sorted(xs)
+    return xs[min(len(xs) - 1, int(q * len(xs)))] if xs else None
+
+
+def _plain_service_times(L, packed, max_size, cache):
+    """Each problem alone through the plain path (create, solve, destroy), warm
+    allocator: (status, size, seconds) per problem."""
+    import torch
+    cfg = L.torch_config(cache_bytes=cache)
+    out = []
+    for q in packed:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with L.Synthesizer(q, cfg) as s:
+            st, res, f, _ = s.solve(max_size)
+        torch.cuda.synchronize()
+        out.append((st, res.size, time.perf_counter() - t0))
+    return out
+
+
+def run_batched(args):
+    import torch
+    world, rank, local = _dist()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    from paper_2504_18943_gb300 import build
+    build.build()
+    from paper_2504_18943_gb300 import lsyn as L
+    from paper_2504_18943_gb300 import workloads as W
+    packed = _batched_problems(L, W)
+    cfg = L.make_config(cache_bytes=BATCH_CACHE, device=local)
+    b = L.Batch(packed, cfg)
+    tuned = b.autotune(BATCH_MAX_SIZE) if args.autotune else None  # chooses the launch shape (counts as warm-up)
+    for _ in range(args.warmup):
+        b.solve(BATCH_MAX_SIZE)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    total_ms, lat, statuses = 0.0, [], None
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:  # noqa: BLE001
+        gpu_id = str(local)
+    with ClockSampler(gpu_id) as clocks:
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            ev0.record()
+            statuses, results, formulas = b.solve(BATCH_MAX_SIZE)
+            ev1.record()
+            torch.cuda.synchronize()
+            total_ms += ev0.elapsed_time(ev1)
+            lat += [r.ms for r in results]
+    stats, trace = b.stats(), b.trace()
+    b.close()
+    max_ms = _reduce_max(total_ms, world)
+    value = world * BATCH_N * args.steps / (max_ms / 1000.0)
+    # end to end through the public API: create from host arrays, solve, read answers, destroy
+    t0 = time.perf_counter()
+    with L.Batch(packed, cfg, tuned) as b2:
+        b2.solve(BATCH_MAX_SIZE)
+    e2e_s = time.perf_counter() - t0
+    plain = _plain_service_times(L, packed, BATCH_MAX_SIZE, BATCH_CACHE) if not args.no_plain else None
+    line = None
+    if rank == 0:
+        same = None
+        plain_d = None
+        if plain:
+            same = all((statuses[i] == plain[i][0]) for i in range(BATCH_N))
+            t_all = sum(p[2] for p in plain)
+            finish, acc = [], 0.0
+            for p in plain:
+                acc += p[2]
+                finish.append(acc * 1000.0)
+            plain_d = {"problems_per_s": BATCH_N / t_all, "total_s": t_all,
+                       "p50_ms": _percentile(finish, 0.5), "p99_ms": _percentile(finish, 0.99),
+                       "how": "each problem alone through lsyn_create + lsyn_solve + lsyn_destroy, one after another "
+                              "(time-to-formula = its finish time when all 256 arrive at once)"}
+        steps_tr = [t for t in trace if t["lane"] == 0]
+        large_tr = [t for t in trace if t["lane"] == 1]
+        line = {
+            "metric": "problems/sec", "value": value, "unit": "problems/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": BATCH_WORKLOAD, "problems": BATCH_N, "max_size": BATCH_MAX_SIZE,
+                       "l2_flush": False, "inputs": "caches far larger than L2 (GBs per step)"},
+            "p50_ms": _percentile(lat, 0.5), "p99_ms": _percentile(lat, 0.99),
+            "statuses": {str(k): statuses.count(k) for k in sorted(set(statuses))},
+            "plain_serial": plain_d, "same_answers_as_plain": same,
+            "vs_plain": (value / plain_d["problems_per_s"]) if plain_d else None,
+            "tuning": {k: getattr(tuned, k) for k, _ in tuned._fields_} if tuned else None,
+            "sched": stats,
+            "trace_totals": {"batch_steps": len(steps_tr), "large_levels": len(large_tr),
+                             "host_ms": sum(t["plan_ms"] + t["settle_ms"] for t in trace)},
+            "roofline": None, "roofline_note": "the level kernels' roofline is reported by the default (mid) workload",
+            "e2e": {"value": BATCH_N / e2e_s, "unit": "problems/s",
+                    "h2d_bytes_per_step": sum(q.h2d_bytes for q in packed), "d2h_bytes_per_step": BATCH_N * 4096},
+            "gpu_launches": None, "clocks": clocks.summary(),
+        }
+        print(json.dumps(line))
+    return 0
+
+
+def run_served(args):
+    import torch
+    world, rank, local = _dist()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    from paper_2504_18943_gb300 import build
+    build.build()
+    from paper_2504_18943_gb300 import lsyn as L
+    from paper_2504_18943_gb300 import workloads as W
+    packed = _batched_problems(L, W)
+    plain = _plain_service_times(L, packed, BATCH_MAX_SIZE, BATCH_CACHE)
+    cfg = L.make_config(cache_bytes=BATCH_CACHE, device=local)
+    rates = [float(r) for r in args.rates.split(",")]
+    out = []
+    for rate in rates:
+        arrivals = W.poisson_arrivals(0, rate, args.duration)
+        order = [i % BATCH_N for i in range(len(arrivals))]
+        with L.Server(cfg) as sv:
+            for q in packed[:8]:  # warm the pool and the launch paths
+                sv.wait(sv.submit(q, BATCH_MAX_SIZE))
+            tickets = [None] * len(arrivals)
+            t0 = time.perf_counter()
+            for i, (ta, pi) in enumerate(zip(arrivals, order)):
+                d = t0 + ta - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                tickets[i] = sv.submit(packed[pi], BATCH_MAX_SIZE)
+            res = [sv.wait(t) for t in tickets]
+            t_end = time.perf_counter()
+            stats = sv.stats()
+        lat = [r[1].ms for r in res]
+        wrong = sum(1 for (st, r, f), pi in zip(res, order) if (st, r.size if st == 0 else 0) !=
+                    (plain[pi][0], plain[pi][1] if plain[pi][0] == 0 else 0))
+        # The plain path as one serial FIFO server: each arrival waits for the
+        # previous problems, then takes its measured one-problem time.
+        free_at, plat = 0.0, []
+        for ta, pi in zip(arrivals, order):
+            start = max(ta, free_at)
+            free_at = start + plain[pi][2]
+            plat.append((free_at - ta) * 1000.0)
+        out.append({"rate": rate, "submitted": len(arrivals), "problems_per_s": len(arrivals) / (t_end - t0),
+                    "p50_ms": _percentile(lat, 0.5), "p99_ms": _percentile(lat, 0.99), "answers_differ": wrong,
+                    "plain_serial": {"problems_per_s": len(arrivals) / max(free_at, arrivals[-1]),
+                                     "p50_ms": _percentile(plat, 0.5), "p99_ms": _percentile(plat, 0.99)},
+                    "sched": {k: stats[k] for k in ("steps", "large_levels", "evictions", "redos", "pool_peak")}})
+    if rank == 0:
+        top = out[-1]
+        line = {
+            "metric": "problems/sec, p50/p99 time-to-formula", "value": top["problems_per_s"], "unit": "problems/s",
+            "n_gpus": world, "steps": len(rates), "warmup": 8, "ms_per_step": 1000.0 * args.duration,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "served: open-loop Poisson arrivals (seeded) of the 256 batched problems in "
+                                   "turn, max size 13, 8 GiB cap each", "rates": rates, "duration_s": args.duration},
+            "per_rate": out,
+            "plain_serial_how": "a FIFO queue served by the one-problem path, each problem taking its measured "
+                                "lsyn_create + lsyn_solve + lsyn_destroy time",
+            "roofline": None, "roofline_note": "the level kernels' roofline is reported by the default (mid) workload",
+            "e2e": {"value": top["problems_per_s"], "unit": "problems/s",
+                    "h2d_bytes_per_step": None, "d2h_bytes_per_step": None},
+            "gpu_launches": None,
+        }
+        print(json.dumps(line))
+    return 0
+
+
 def _kernel_sha() -> str:
     import hashlib
     h = hashlib.sha256()
@@ -342,9 +526,20 @@ def main():
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--ref-levels", type=int, default=7)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="mid", choices=["mid", "batched", "served"],
+                    help="mid (default): the one-problem headline; batched: 256 problems per step; "
+                         "served: Poisson arrivals through the server")
+    ap.add_argument("--autotune", action="store_true", help="batched: run the autotuner before timing")
+    ap.add_argument("--no-plain", action="store_true", help="batched: skip the plain-path comparison")
+    ap.add_argument("--rates", default="50,200,1000", help="served: arrival rates (problems/s)")
+    ap.add_argument("--duration", type=float, default=60.0, help="served: seconds of arrivals per rate")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "served":
+        return run_served(args)
     return run_lsyn(args)
 
 

@@ -244,6 +244,14 @@ lsyn_status lsyn_eval(const lsyn_problem* problem, const char* formula, void* ds
  * every admitted problem (the listing of "A generic program synthesiser"
  * applied to each problem).
  *
+ * Two lanes share the GPU: small levels of every admitted problem advance in
+ * batch steps (one persistent launch each) on a high-priority stream, while a
+ * level with more than solo_candidates candidates runs in the large-level lane
+ * (the one-problem kernels on streams of their own, on all but light_sms SMs;
+ * up to `lanes` problems' levels at once, taken in admission order). A step
+ * never waits for a large level, so small problems are not held up by large
+ * ones.
+ *
  * Memory: per-problem language caches live in one device memory pool
  * (pool_bytes). A cache starts small and grows before each level to the
  * entries the level is predicted to add, without copying (virtual address
@@ -265,8 +273,10 @@ typedef struct {
   int32_t predict_pct;    /* a level's predicted new entries: candidates x this percentage of the
                              previous level's unique ratio (0 = 150); lower saves memory, costs redos */
   uint64_t pool_bytes;    /* device memory for every cache together (0: 90% of the free memory) */
-  uint64_t solo_candidates; /* a level with more candidates runs as launches of its own with the
-                               one-problem kernels inside the step (0 = 2^19) */
+  uint64_t solo_candidates; /* a level with more candidates is a large level: it runs in the large-level
+                               lane with the one-problem kernels, beside the batch steps (0 = 2^19) */
+  int32_t light_sms;      /* SMs the batch steps keep while a large level runs (0 = 1/8 of the SMs) */
+  int32_t lanes;          /* large levels of different problems in flight at once (0 = 4) */
 } lsyn_batch_tuning;
 
 typedef struct {
@@ -274,9 +284,29 @@ typedef struct {
   int64_t steps;          /* batch steps run */
   int64_t evictions;      /* problems evicted and restarted for lack of memory */
   int64_t redos;          /* levels undone and run again (outgrew their prediction) */
-  int64_t reserved0;
+  int64_t large_levels;   /* levels run in the large-level lane */
   uint64_t pool_bytes, pool_in_use, pool_peak;
 } lsyn_sched_stats;
+
+/*
+ * One unit of scheduler work (a trace for tuning; the last 4096 are kept):
+ * a batch step (lane 0) or one large level (lane 1; times are as the host saw
+ * them between steps).
+ */
+typedef struct {
+  int64_t step;           /* batch steps run before it */
+  int32_t lane;           /* 0: batch step, 1: large level */
+  int32_t active;         /* problems advanced (1 for a large level) */
+  int32_t solo;           /* batch step: a large level was in flight beside it */
+  int32_t passes;         /* deferred-candidate passes */
+  int32_t finished;       /* problems answered */
+  int32_t level;          /* large level: its size k */
+  double plan_ms;         /* host: predictions, cache growth, table rebuild launches */
+  double run_ms;          /* the launches until their counters are back */
+  double settle_ms;       /* deferred passes, hole fixups, commits, answers */
+  uint64_t candidates;    /* candidates built */
+  uint64_t pool_in_use;
+} lsyn_step_trace;
 
 /*
  * Batched solving of n independent specifications.
@@ -306,9 +336,11 @@ lsyn_status lsyn_batch_create(const lsyn_problem* problems, int32_t n, const lsy
 lsyn_status lsyn_batch_solve(lsyn_batch* batch, int32_t max_size, lsyn_result* results, int32_t* statuses);
 
 /*
- * Autotuner: solves the batch (up to max_size) once per candidate launch shape
- * (blocks per SM in {2, 4, 6, 8}, with and without the step graphs), keeps the
- * fastest for later lsyn_batch_solve calls and writes it to *out (may be NULL).
+ * Autotuner: solves the batch (up to max_size) repeatedly, one parameter at a
+ * time over blocks per SM {2, 4, 8}, step graphs {off, on}, solo_candidates
+ * {2^17, 2^19, 2^21} and light_sms {1/16, 1/8, 1/4 of the SMs}, keeping the
+ * fastest value of each; the result serves later lsyn_batch_solve calls and
+ * is written to *out (may be NULL).
  */
 lsyn_status lsyn_batch_autotune(lsyn_batch* batch, int32_t max_size, lsyn_batch_tuning* out);
 
@@ -322,6 +354,9 @@ lsyn_status lsyn_batch_autotune(lsyn_batch* batch, int32_t max_size, lsyn_batch_
 lsyn_status lsyn_batch_problem(lsyn_batch* batch, int32_t i, lsyn_ctx** out);
 
 lsyn_status lsyn_batch_stats(const lsyn_batch* batch, lsyn_sched_stats* out);
+
+/* The step trace of the last lsyn_batch_solve: up to cap entries into out, their count in *n_out. */
+lsyn_status lsyn_batch_trace(const lsyn_batch* batch, lsyn_step_trace* out, int32_t cap, int32_t* n_out);
 
 /* Message of the last error of the batch (NULL: of the last failed lsyn_batch_create on this thread). */
 const char* lsyn_batch_last_error(const lsyn_batch* batch);
@@ -367,6 +402,9 @@ lsyn_status lsyn_poll(lsyn_server* server, uint64_t ticket, lsyn_result* out);
 lsyn_status lsyn_wait(lsyn_server* server, uint64_t ticket, int32_t timeout_ms, lsyn_result* out);
 
 lsyn_status lsyn_server_stats(lsyn_server* server, lsyn_sched_stats* out);
+
+/* The server's most recent steps (oldest first): up to cap entries into out, their count in *n_out. */
+lsyn_status lsyn_server_trace(lsyn_server* server, lsyn_step_trace* out, int32_t cap, int32_t* n_out);
 
 /* Message of the server's last error (NULL: of the last failed lsyn_server_create on this thread). */
 const char* lsyn_server_last_error(const lsyn_server* server);

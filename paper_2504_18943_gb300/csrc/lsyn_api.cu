@@ -57,8 +57,8 @@ __global__ void k_level_begin(DevCounters* c) {
   c->sol = ~0ull;
 }
 
-__global__ void k_reconstruct(const unsigned long long* prov, unsigned long long root,
-                              const unsigned long long* root_ptr, char* buf, unsigned cap, int* status) {
+__device__ void reconstruct_one(const unsigned long long* prov, unsigned long long root,
+                                const unsigned long long* root_ptr, char* buf, unsigned cap, int* status) {
   const char kOp[8] = {'p', '!', '&', '|', 'X', 'F', 'G', 'U'};
   struct Frame {
     unsigned long long d;
@@ -108,6 +108,18 @@ __global__ void k_reconstruct(const unsigned long long* prov, unsigned long long
   *status = bad;
 }
 
+__global__ void k_reconstruct(const unsigned long long* prov, unsigned long long root,
+                              const unsigned long long* root_ptr, char* buf, unsigned cap, int* status) {
+  reconstruct_one(prov, root, root_ptr, buf, cap, status);
+}
+
+// One formula per block (thread 0): item i writes buf + i * cap and status[i].
+__global__ void k_reconstruct_many(const lsyn::FormulaItem* items, int n, char* buf, unsigned cap, int* status) {
+  const int i = blockIdx.x;
+  if (i >= n || threadIdx.x != 0) return;
+  reconstruct_one(items[i].prov, 0, items[i].root, buf + size_t(i) * cap, cap, status + i);
+}
+
 // Candidates built at level k given the sizes of levels 1..k-1 (sizes[i-1]).
 int64_t level_candidates(const int64_t* sizes, int k, uint32_t mask) {
   if (k < 2) return 0;
@@ -130,6 +142,18 @@ lsyn_status launch_desc(lsyn_ctx* c, const CacheView& cv, const unsigned long lo
 }
 
 }  // namespace
+
+cudaError_t lsyn::launch_level_begin(DevCounters* c, cudaStream_t stream) {
+  k_level_begin<<<1, 1, 0, stream>>>(c);
+  return cudaGetLastError();
+}
+
+cudaError_t lsyn::reconstruct_many(const FormulaItem* items, int n, char* buf, unsigned cap, int* status,
+                                   cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  k_reconstruct_many<<<n, 32, 0, stream>>>(items, n, buf, cap, status);
+  return cudaGetLastError();
+}
 
 lsyn_status lsyn::ctx_reconstruct(lsyn_ctx* c, const unsigned long long* root_ptr, char* out, size_t cap) {
   k_reconstruct<<<1, 1, 0, c->stream>>>(c->prov, 0, root_ptr, c->fbuf, lsyn_ctx::kFormulaCap, c->fstatus);

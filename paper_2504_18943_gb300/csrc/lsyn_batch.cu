@@ -38,6 +38,15 @@ lsyn_status lsyn_batch_problem(lsyn_batch* b, int32_t i, lsyn_ctx** out) {
   return LSYN_OK;
 }
 
+lsyn_status lsyn_batch_trace(const lsyn_batch* b, lsyn_step_trace* out, int32_t cap, int32_t* n_out) {
+  if (!b || !n_out || cap < 0 || (cap > 0 && !out)) return LSYN_E_INVAL;
+  const std::vector<lsyn_step_trace> t = b->eng.trace();
+  const size_t n = std::min(t.size(), size_t(cap));
+  for (size_t i = 0; i < n; ++i) out[i] = t[i];
+  *n_out = int32_t(n);
+  return LSYN_OK;
+}
+
 const char* lsyn_batch_last_error(const lsyn_batch* b) { return b ? b->err.c_str() : g_batch_error.c_str(); }
 
 lsyn_status lsyn_batch_stats(const lsyn_batch* b, lsyn_sched_stats* out) {
@@ -52,6 +61,7 @@ lsyn_status lsyn_batch_stats(const lsyn_batch* b, lsyn_sched_stats* out) {
   out->steps = int64_t(b->eng.steps_run());
   out->evictions = int64_t(b->eng.evictions());
   out->redos = int64_t(b->eng.redos());
+  out->large_levels = int64_t(b->eng.large_levels());
   out->pool_bytes = b->eng.pool().budget();
   out->pool_in_use = b->eng.pool().in_use();
   out->pool_peak = b->eng.peak_in_use();
@@ -97,6 +107,7 @@ lsyn_status lsyn_batch_solve(lsyn_batch* b, int32_t max_size, lsyn_result* resul
   }
   b->err.clear();
   b->eng.clear();  // drop the caches of an earlier solve
+  b->eng.clear_trace();
   const double t0 = now_ms();
   const uint64_t steps0 = b->eng.steps_run();
   for (size_t i = 0; i < b->jobs.size(); ++i) {
@@ -113,8 +124,9 @@ lsyn_status lsyn_batch_solve(lsyn_batch* b, int32_t max_size, lsyn_result* resul
     b->eng.enqueue(j, t0);
   }
   while (b->eng.busy()) {
+    bool moved = false;
     lsyn_status s = b->eng.admit();
-    if (s == LSYN_OK) s = b->eng.step();
+    if (s == LSYN_OK) s = b->eng.pump(true, &moved);
     if (s != LSYN_OK) {
       b->err = b->eng.err;
       b->eng.clear();
@@ -161,18 +173,41 @@ lsyn_status lsyn_batch_autotune(lsyn_batch* b, int32_t max_size, lsyn_batch_tuni
     res[i].formula_cap = fbuf[i].size();
   }
   const lsyn_batch_tuning saved = b->eng.tune();
+  auto time_it = [&](const lsyn_batch_tuning& t, double* ms) {
+    b->eng.set_tune(t);
+    const double t0 = now_ms();
+    lsyn_status s = lsyn_batch_solve(b, max_size, res.data(), st.data());
+    *ms = now_ms() - t0;
+    return s;
+  };
+  // one untimed solve warms the pool and the launch paths
+  double ms = 0;
+  lsyn_status s = time_it(saved, &ms);
+  if (s != LSYN_OK) return s;
   lsyn_batch_tuning best = saved;
   double best_ms = 1e300;
-  for (int g = 0; g < 2; ++g) {
-    for (int bl : {2, 4, 6, 8}) {
-      lsyn_batch_tuning t = saved;
-      t.blocks_per_sm = bl;
-      t.use_graph = g;
-      b->eng.set_tune(t);
-      const double t0 = now_ms();
-      lsyn_status s = lsyn_batch_solve(b, max_size, res.data(), st.data());
-      const double ms = now_ms() - t0;
-      if (s != LSYN_OK) {
+  if ((s = time_it(best, &best_ms)) != LSYN_OK) return s;
+  int sms = 1;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+  // coordinate descent: one parameter at a time, keep the fastest value
+  const int32_t blocks[3] = {2, 4, 8};
+  const uint64_t solo[3] = {1ull << 17, 1ull << 19, 1ull << 21};
+  const int32_t light[3] = {std::max(1, sms / 16), std::max(1, sms / 8), std::max(1, sms / 4)};
+  for (int axis = 0; axis < 4; ++axis) {
+    std::vector<lsyn_batch_tuning> cand;
+    for (int v = 0; v < 3; ++v) {
+      lsyn_batch_tuning t = best;
+      if (axis == 0) t.blocks_per_sm = blocks[v];
+      if (axis == 1) {
+        if (v == 2) continue;
+        t.use_graph = v;
+      }
+      if (axis == 2) t.solo_candidates = solo[v];
+      if (axis == 3) t.light_sms = light[v];
+      cand.push_back(t);
+    }
+    for (const lsyn_batch_tuning& t : cand) {
+      if ((s = time_it(t, &ms)) != LSYN_OK) {
         b->eng.set_tune(saved);
         return s;
       }

@@ -203,5 +203,16 @@ lsyn_status ctx_commit_level(lsyn_ctx* c, int k, const DevCounters& h, uint32_t 
                              const LevelPlan& lp, lsyn_level_stats* out);
 // Write the formula of descriptor *root_ptr (device) into out.
 lsyn_status ctx_reconstruct(lsyn_ctx* c, const unsigned long long* root_ptr, char* out, size_t cap);
+// Formula text of n descriptors in one launch: item i (device array) names a
+// provenance array and the device word holding the root descriptor; its text
+// goes to buf + i * cap (device), status[i] = 0 if it fit.
+struct FormulaItem {
+  const unsigned long long* prov;
+  const unsigned long long* root;
+};
+// Clear the per-level counters (as the start of lsyn_enumerate_level does).
+cudaError_t launch_level_begin(DevCounters* c, cudaStream_t stream);
+cudaError_t reconstruct_many(const FormulaItem* items, int n, char* buf, unsigned cap, int* status,
+                             cudaStream_t stream);
 double now_ms();
 }  // namespace lsyn

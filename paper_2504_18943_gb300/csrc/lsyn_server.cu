@@ -13,6 +13,8 @@
 #include <string>
 #include <thread>
 #include <unordered_map>
+#include <vector>
+#include <algorithm>
 
 #include "lsyn.h"
 #include "lsyn_engine.h"
@@ -31,6 +33,7 @@ struct lsyn_server {
   lsyn_status fatal = LSYN_OK;
   std::string err;
   lsyn_sched_stats stats{};
+  std::vector<lsyn_step_trace> trace;  // snapshot of the engine's trace, updated by the loop
   std::thread th;
   int device = 0;
 
@@ -61,6 +64,7 @@ lsyn_status deliver(const Job& j, lsyn_result* out) {
 
 void lsyn_server::loop() {
   cudaSetDevice(device);
+  int64_t last_steps = 0;
   while (true) {
     {
       std::unique_lock<std::mutex> lk(mu);
@@ -73,10 +77,11 @@ void lsyn_server::loop() {
         running[j->ticket] = std::move(j);
       }
     }
+    bool moved = false;
     lsyn_status s = eng.admit();
-    if (s == LSYN_OK && eng.busy()) s = eng.step();
+    if (s == LSYN_OK && eng.busy()) s = eng.pump(false, &moved);
     std::vector<Job*> done = eng.take_done();
-    std::lock_guard<std::mutex> lk(mu);
+    std::unique_lock<std::mutex> lk(mu);
     for (Job* j : done) {
       auto it = running.find(j->ticket);
       if (it == running.end()) continue;
@@ -89,8 +94,13 @@ void lsyn_server::loop() {
     stats.steps = int64_t(eng.steps_run());
     stats.evictions = int64_t(eng.evictions());
     stats.redos = int64_t(eng.redos());
+    stats.large_levels = int64_t(eng.large_levels());
     stats.pool_in_use = eng.pool().in_use();
     stats.pool_peak = eng.peak_in_use();
+    if (stats.steps != last_steps) {
+      trace = eng.trace();
+      last_steps = stats.steps;
+    }
     if (s != LSYN_OK) {
       fatal = s;
       err = eng.err;
@@ -99,6 +109,9 @@ void lsyn_server::loop() {
       return;
     }
     if (!done.empty()) cv_done.notify_all();
+    // Only a large level is in flight: look again shortly, or at once if a
+    // submission arrives (it may join the batch steps meanwhile).
+    if (!moved && done.empty()) cv_work.wait_for(lk, std::chrono::microseconds(100), [&] { return stop || !inbox.empty(); });
   }
 }
 
@@ -206,6 +219,15 @@ lsyn_status lsyn_wait(lsyn_server* sv, uint64_t ticket, int32_t timeout_ms, lsyn
     }
   }
   return lsyn_poll(sv, ticket, out);
+}
+
+lsyn_status lsyn_server_trace(lsyn_server* sv, lsyn_step_trace* out, int32_t cap, int32_t* n_out) {
+  if (!sv || !n_out || cap < 0 || (cap > 0 && !out)) return LSYN_E_INVAL;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  const size_t n = std::min(sv->trace.size(), size_t(cap));
+  for (size_t i = 0; i < n; ++i) out[i] = sv->trace[sv->trace.size() - n + i];
+  *n_out = int32_t(n);
+  return LSYN_OK;
 }
 
 lsyn_status lsyn_server_stats(lsyn_server* sv, lsyn_sched_stats* out) {

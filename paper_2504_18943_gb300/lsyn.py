@@ -73,24 +73,35 @@ class lsyn_result(ctypes.Structure):
 class lsyn_batch_tuning(ctypes.Structure):
     _fields_ = [("blocks_per_sm", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("max_active", ctypes.c_int32),
                 ("predict_pct", ctypes.c_int32), ("pool_bytes", ctypes.c_uint64),
-                ("solo_candidates", ctypes.c_uint64)]
+                ("solo_candidates", ctypes.c_uint64), ("light_sms", ctypes.c_int32), ("lanes", ctypes.c_int32)]
 
 
 class lsyn_sched_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("active", ctypes.c_int64),
                 ("queued", ctypes.c_int64), ("steps", ctypes.c_int64), ("evictions", ctypes.c_int64),
-                ("redos", ctypes.c_int64), ("reserved0", ctypes.c_int64), ("pool_bytes", ctypes.c_uint64),
+                ("redos", ctypes.c_int64), ("large_levels", ctypes.c_int64), ("pool_bytes", ctypes.c_uint64),
                 ("pool_in_use", ctypes.c_uint64), ("pool_peak", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
 
 
+class lsyn_step_trace(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_int64), ("lane", ctypes.c_int32), ("active", ctypes.c_int32),
+                ("solo", ctypes.c_int32), ("passes", ctypes.c_int32), ("finished", ctypes.c_int32),
+                ("level", ctypes.c_int32), ("plan_ms", ctypes.c_double), ("run_ms", ctypes.c_double),
+                ("settle_ms", ctypes.c_double), ("candidates", ctypes.c_uint64), ("pool_in_use", ctypes.c_uint64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 def make_tuning(blocks_per_sm: int = 0, use_graph: int = 0, max_active: int = 0, pool_bytes: int = 0,
-                predict_pct: int = 0, solo_candidates: int = 0) -> lsyn_batch_tuning:
+                predict_pct: int = 0, solo_candidates: int = 0, light_sms: int = 0, lanes: int = 0
+                ) -> lsyn_batch_tuning:
     t = lsyn_batch_tuning()
     t.blocks_per_sm, t.use_graph, t.max_active, t.pool_bytes = blocks_per_sm, use_graph, max_active, pool_bytes
-    t.predict_pct, t.solo_candidates = predict_pct, solo_candidates
+    t.predict_pct, t.solo_candidates, t.light_sms, t.lanes = predict_pct, solo_candidates, light_sms, lanes
     return t
 
 
@@ -146,6 +157,10 @@ def _load_library():
     lib.lsyn_batch_destroy.argtypes = [vp]
     lib.lsyn_batch_stats.restype = i32
     lib.lsyn_batch_stats.argtypes = [vp, P(lsyn_sched_stats)]
+    lib.lsyn_batch_trace.restype = i32
+    lib.lsyn_batch_trace.argtypes = [vp, P(lsyn_step_trace), i32, P(i32)]
+    lib.lsyn_server_trace.restype = i32
+    lib.lsyn_server_trace.argtypes = [vp, P(lsyn_step_trace), i32, P(i32)]
     lib.lsyn_server_create.restype = i32
     lib.lsyn_server_create.argtypes = [P(lsyn_config), P(lsyn_batch_tuning), P(vp)]
     lib.lsyn_submit.restype = i32
@@ -502,6 +517,21 @@ def lsyn_batch_destroy(batch) -> None:
     _lib.lsyn_batch_destroy(batch)
 
 
+def _trace(fn, handle, cap: int = 4096) -> list:
+    buf = (lsyn_step_trace * cap)()
+    n = ctypes.c_int32()
+    _check(fn(handle, buf, cap, ctypes.byref(n)), None)
+    return [buf[i].as_dict() for i in range(n.value)]
+
+
+def lsyn_batch_trace(batch) -> list:
+    return _trace(_lib.lsyn_batch_trace, batch)
+
+
+def lsyn_server_trace(server) -> list:
+    return _trace(_lib.lsyn_server_trace, server)
+
+
 def lsyn_batch_stats(batch) -> dict:
     st = lsyn_sched_stats()
     _check(_lib.lsyn_batch_stats(batch, ctypes.byref(st)), None)
@@ -549,6 +579,9 @@ class Batch:
 
     def stats(self) -> dict:
         return lsyn_batch_stats(self.handle)
+
+    def trace(self) -> list:
+        return lsyn_batch_trace(self.handle)
 
 
 # ---------------------------------------------------------------------------
@@ -645,3 +678,6 @@ class Server:
 
     def stats(self) -> dict:
         return lsyn_server_stats(self.handle)
+
+    def trace(self) -> list:
+        return lsyn_server_trace(self.handle)

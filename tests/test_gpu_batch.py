@@ -137,3 +137,23 @@ def test_underpredicted_levels_are_redone(L, problems):
                 assert statuses[i] == st
                 for k in _complete_levels(st, res):
                     assert np.array_equal(canon(b.export(i, k)), canon(s.export(k))), (i, k)
+
+
+def test_large_level_lane_matches_plain(L, problems):
+    """With a low threshold most levels run in the large-level lane (one-problem
+    kernels on their own stream, beside the batch steps on a few SMs); answers
+    and complete levels stay those of the plain path."""
+    packed = [L.pack_problem(p) for p in problems]
+    cfg = L.make_config(cache_bytes=1 << 30)
+    with L.Batch(packed, cfg, L.make_tuning(solo_candidates=2000, light_sms=8)) as b:
+        got = b.solve(9)
+        assert b.stats()["large_levels"] > 0
+        _assert_matches_plain(L, problems, packed, got, cfg, 9)
+        statuses, results, _ = got
+        for i in range(len(packed)):
+            if statuses[i] not in (L.LSYN_OK, L.LSYN_NOT_FOUND):
+                continue
+            with L.Synthesizer(packed[i], cfg) as s:
+                st, res, f, _ = s.solve(9)
+                for k in _complete_levels(st, res):
+                    assert np.array_equal(canon(b.export(i, k)), canon(s.export(k))), (i, k)
