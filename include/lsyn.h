@@ -365,6 +365,46 @@ const char* lsyn_batch_last_error(const lsyn_batch* batch);
 void lsyn_batch_destroy(lsyn_batch* batch);
 
 /*
+ * Divide-and-conquer (paragraph "Divide-and-conquer"): a specification with no
+ * separating formula of size <= max_size that fits its cache is split into
+ * four parts (P_i, N_j), i, j = 1, 2 — P_1 the first ceil(|P| / 2) positive
+ * traces, P_2 the rest, N_1 and N_2 likewise — the parts are solved
+ * recursively and recombined as (phi_11 & phi_12) | (phi_21 & phi_22). A part
+ * with a single positive trace splits N only (phi_1 & phi_2); one with a
+ * single negative trace splits P only (phi_1 | phi_2). The parts pending at
+ * each depth are solved together, as one batch of the scheduler above.
+ *   problem    as for lsyn_create (copied); max_size 1..17 for every part.
+ *   config     per-part settings (cache_bytes = each part's cap); tuning as
+ *              for a batch (NULL = defaults).
+ *   out        found / size (nodes of the returned formula) / formula text
+ *              (caller's buffer) / ms / constructed and unique (summed over
+ *              every part solved); exact = 1 only if no split was needed
+ *              (the answer is then minimal; otherwise it separates but need
+ *              not be minimal).
+ *   stats      may be NULL.
+ * Returns LSYN_OK, LSYN_NOT_FOUND if a part of one positive and one negative
+ * trace has no separating formula up to max_size (for example two equal
+ * traces), LSYN_E_INVAL (bad problem or max_size, or out->formula too small:
+ * out->formula_cap is then not changed and the needed length is in
+ * stats->formula_len), or an error of the scheduler.
+ */
+typedef struct {
+  int32_t rounds;         /* depths solved */
+  int32_t splits;         /* parts that were split */
+  int32_t leaves;         /* parts answered directly */
+  int32_t depth;          /* deepest part (0 = the whole specification) */
+  int64_t parts;          /* parts solved in all */
+  int64_t formula_len;    /* length of the combined formula text */
+  int64_t reserved[2];
+} lsyn_dc_stats;
+
+lsyn_status lsyn_dc_solve(const lsyn_problem* problem, int32_t max_size, const lsyn_config* config,
+                          const lsyn_batch_tuning* tuning, lsyn_result* out, lsyn_dc_stats* stats);
+
+/* Message of this thread's last failed lsyn_dc_solve. */
+const char* lsyn_dc_last_error(void);
+
+/*
  * Serving: a host thread runs the step loop over the problems submitted so
  * far. A submission joins the loop between steps as soon as a slot and pool
  * memory allow (admission in submission order, by the memory the running

@@ -208,3 +208,70 @@ def labeller(formula: str, traces, n_props: int) -> np.ndarray:
     s = Spec(n_props, traces.lengths, masks.astype(np.int32), len(traces.lengths))
     cm = s.eval_seq(formula)  # bottom-up, O(length^2) per node; pinned equal to the recursive definition
     return np.array([seq[:1] == "1" for seq in cm.split(",")], dtype=bool)
+
+
+def dc_solve(problem, max_size: int, op_mask: int = ALL_OPS):
+    """Divide-and-conquer (paragraph "Divide-and-conquer" of section "Parallel
+    enumeration of LTLf formulae on GPUs"), on the oracle's exact solver.
+
+    A specification (P, N) that has a separating formula of size <= max_size is
+    answered by it (``Spec.solve``). Otherwise it is split into (P_i, N_j),
+    i, j = 1, 2, with P the disjoint union of P_1 and P_2 and N of N_1 and N_2,
+    the phi_ij are synthesised recursively from the (P_i, N_j), and the answer
+    is (phi_11 and phi_12) or (phi_21 and phi_22). Readings where the paragraph
+    is silent: P_1 is the first ceil(|P| / 2) positives in input order and P_2
+    the rest (N likewise); a part with one positive trace splits N only
+    (phi_1 and phi_2), one with one negative trace splits P only
+    (phi_1 or phi_2); a part of one positive and one negative trace without an
+    answer has none.
+
+    Returns (size, formula, stats): size 0 and formula None when some part has
+    no answer; stats counts splits, leaves and the deepest part.
+    """
+    lengths = np.asarray(problem.traces.lengths, dtype=np.int32)
+    masks = problem.position_masks()
+    n_props = problem.n_props
+    stats = {"splits": 0, "leaves": 0, "depth": 0}
+
+    def halves(v):
+        h = (len(v) + 1) // 2
+        return v[:h], v[h:]
+
+    def solve(pos, neg, depth):
+        stats["depth"] = max(stats["depth"], depth)
+        idx = pos + neg
+        spec = Spec(n_props, lengths[idx], masks[idx], len(pos))
+        size, formula, _ = spec.solve(max_size, op_mask)
+        if size > 0:
+            stats["leaves"] += 1
+            return size, formula
+        if len(pos) >= 2 and len(neg) >= 2:
+            (p1, p2), (n1, n2) = halves(pos), halves(neg)
+            parts = [solve(p1, n1, depth + 1), solve(p1, n2, depth + 1),
+                     solve(p2, n1, depth + 1), solve(p2, n2, depth + 1)]
+            if any(x is None for x in parts):
+                return None
+            stats["splits"] += 1
+            (s11, f11), (s12, f12), (s21, f21), (s22, f22) = parts
+            return 3 + s11 + s12 + s21 + s22, f"(| (& {f11} {f12}) (& {f21} {f22}))"
+        if len(pos) >= 2:
+            p1, p2 = halves(pos)
+            parts = [solve(p1, neg, depth + 1), solve(p2, neg, depth + 1)]
+            if any(x is None for x in parts):
+                return None
+            stats["splits"] += 1
+            return 1 + parts[0][0] + parts[1][0], f"(| {parts[0][1]} {parts[1][1]})"
+        if len(neg) >= 2:
+            n1, n2 = halves(neg)
+            parts = [solve(pos, n1, depth + 1), solve(pos, n2, depth + 1)]
+            if any(x is None for x in parts):
+                return None
+            stats["splits"] += 1
+            return 1 + parts[0][0] + parts[1][0], f"(& {parts[0][1]} {parts[1][1]})"
+        return None
+
+    T = len(lengths)
+    got = solve(list(range(problem.n_pos)), list(range(problem.n_pos, T)), 0)
+    if got is None:
+        return 0, None, stats
+    return got[0], got[1], stats

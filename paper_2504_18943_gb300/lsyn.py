@@ -96,6 +96,15 @@ class lsyn_step_trace(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class lsyn_dc_stats(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int32), ("splits", ctypes.c_int32), ("leaves", ctypes.c_int32),
+                ("depth", ctypes.c_int32), ("parts", ctypes.c_int64), ("formula_len", ctypes.c_int64),
+                ("reserved", ctypes.c_int64 * 2)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
 def make_tuning(blocks_per_sm: int = 0, use_graph: int = 0, max_active: int = 0, pool_bytes: int = 0,
                 predict_pct: int = 0, solo_candidates: int = 0, light_sms: int = 0, lanes: int = 0
                 ) -> lsyn_batch_tuning:
@@ -161,6 +170,11 @@ def _load_library():
     lib.lsyn_batch_trace.argtypes = [vp, P(lsyn_step_trace), i32, P(i32)]
     lib.lsyn_server_trace.restype = i32
     lib.lsyn_server_trace.argtypes = [vp, P(lsyn_step_trace), i32, P(i32)]
+    lib.lsyn_dc_solve.restype = i32
+    lib.lsyn_dc_solve.argtypes = [P(lsyn_problem), i32, P(lsyn_config), P(lsyn_batch_tuning), P(lsyn_result),
+                                  P(lsyn_dc_stats)]
+    lib.lsyn_dc_last_error.restype = ctypes.c_char_p
+    lib.lsyn_dc_last_error.argtypes = []
     lib.lsyn_server_create.restype = i32
     lib.lsyn_server_create.argtypes = [P(lsyn_config), P(lsyn_batch_tuning), P(vp)]
     lib.lsyn_submit.restype = i32
@@ -582,6 +596,26 @@ class Batch:
 
     def trace(self) -> list:
         return lsyn_batch_trace(self.handle)
+
+
+# ---------------------------------------------------------------------------
+# Divide-and-conquer
+# ---------------------------------------------------------------------------
+
+def lsyn_dc_solve(problem: PackedProblem, max_size: int, config: Optional[lsyn_config] = None,
+                  tuning: Optional[lsyn_batch_tuning] = None, formula_cap: int = 1 << 20):
+    """(status, result, formula, stats): status LSYN_OK or LSYN_NOT_FOUND; the
+    formula separates the specification (minimal when result.exact)."""
+    r = lsyn_result()
+    buf = ctypes.create_string_buffer(formula_cap)
+    r.formula = ctypes.cast(buf, ctypes.c_char_p)
+    r.formula_cap = formula_cap
+    stats = lsyn_dc_stats()
+    st = _lib.lsyn_dc_solve(ctypes.byref(problem.struct), max_size, ctypes.byref(config) if config is not None else None,
+                            ctypes.byref(tuning) if tuning is not None else None, ctypes.byref(r), ctypes.byref(stats))
+    if st not in (LSYN_OK, LSYN_NOT_FOUND):
+        raise LsynError(st, (_lib.lsyn_dc_last_error() or b"").decode())
+    return st, r, (buf.value.decode() if st == LSYN_OK else None), stats.as_dict()
 
 
 # ---------------------------------------------------------------------------
