@@ -80,12 +80,14 @@ typedef enum {
  * GPUs").
  *   n_props     number of atomic propositions, 1..32.
  *   n_pos       |P| >= 0;  n_neg = |N| >= 0;  n_pos + n_neg >= 1.
- *   word_bits   32 or 64: bits per characteristic-sequence word; every trace
- *               must be at most this long.
- *   lengths     host, int32[n_pos + n_neg]: trace lengths, each 1..word_bits.
- *   atom_words  host, [n_props][n_pos + n_neg] words of word_bits bits
- *               (uint32_t or uint64_t), row-major by proposition. Bit t of word
- *               (p, i) is 1 iff p holds at position t of trace i. Bits at
+ *   word_bits   32 or 64: bits per characteristic-sequence word. A trace
+ *               longer than a word takes W = ceil(longest trace / word_bits)
+ *               words (at most 16; the paper's one word per trace when W = 1).
+ *   lengths     host, int32[n_pos + n_neg]: trace lengths, each
+ *               1..16 x word_bits.
+ *   atom_words  host, [n_props][n_pos + n_neg][W] words of word_bits bits
+ *               (uint32_t or uint64_t), row-major. Bit t of word (p, i, w) is 1
+ *               iff p holds at position w x word_bits + t of trace i. Bits at
  *               positions >= lengths[i] are ignored.
  */
 typedef struct {
@@ -179,8 +181,8 @@ typedef struct lsyn_ctx lsyn_ctx;
  * language cache and scratch on the device, copies the traces there and builds
  * nothing yet. *out receives the context, or NULL on error (then
  * lsyn_last_error(NULL) explains). Errors: LSYN_E_INVAL (bad sizes, lengths out
- * of 1..word_bits, more than 2^30 - 2 cache entries requested), LSYN_E_NOMEM,
- * LSYN_E_CUDA.
+ * of 1..16 x word_bits, more than 2^30 - 2 cache entries requested),
+ * LSYN_E_UNSUPPORTED (a CM above 64 KiB), LSYN_E_NOMEM, LSYN_E_CUDA.
  */
 lsyn_status lsyn_create(const lsyn_problem* problem, const lsyn_config* config, lsyn_ctx** out);
 
@@ -219,8 +221,9 @@ lsyn_status lsyn_level_count(const lsyn_ctx* ctx, int32_t k, int64_t* n_out);
 
 /*
  * Copy the CMs of entries [first, first + count) of level k into dst (host):
- * count rows of (n_pos + n_neg) words of word_bits bits, positives first, the
- * rows in the cache's (unspecified, run-dependent) order. cap = bytes of dst.
+ * count rows of (n_pos + n_neg) x W words of word_bits bits (W words per trace
+ * as in lsyn_problem), positives first, the rows in the cache's (unspecified,
+ * run-dependent) order. cap = bytes of dst.
  */
 lsyn_status lsyn_export_level(lsyn_ctx* ctx, int32_t k, int64_t first, int64_t count,
                               void* dst, size_t cap);
@@ -230,9 +233,10 @@ lsyn_status lsyn_entry_formula(lsyn_ctx* ctx, int32_t k, int64_t index, char* bu
 
 /*
  * Evaluate a formula on every trace of a problem (the bitwise operators on the
- * device). dst (host) receives n_pos + n_neg words of word_bits bits: the
- * formula's CM. config may be NULL (defaults). Errors: LSYN_E_INVAL on a parse
- * error, an atom >= n_props or more than 4096 nodes.
+ * device). dst (host) receives (n_pos + n_neg) x W words of word_bits bits
+ * (W words per trace as in lsyn_problem): the formula's CM. config may be NULL
+ * (defaults). Errors: LSYN_E_INVAL on a parse error, an atom >= n_props or more
+ * than 4096 nodes.
  */
 lsyn_status lsyn_eval(const lsyn_problem* problem, const char* formula, void* dst,
                       const lsyn_config* config);
@@ -462,7 +466,8 @@ void lsyn_server_destroy(lsyn_server* server);
  *   atom_words  device, [n_props][n_traces] words of word_bits bits, row-major
  *               by proposition (bit t of word (p, i): p holds at position t of
  *               trace i); bits at positions >= the trace's length are ignored.
- *   lengths     device, int32[n_traces]; each is clamped to 0..word_bits.
+ *   lengths     device, int32[n_traces]; each is clamped to 0..word_bits (one
+ *               word per trace: longer traces need lsyn_eval).
  *   dst         device, n_traces words of word_bits bits: the formula's CM.
  *   stream      cudaStream_t (NULL = legacy default stream); the call only
  *               enqueues work, synchronise the stream before reading dst.

@@ -235,9 +235,14 @@ bool parse_formula(const char* s, int n_props, std::vector<int4>* nodes, std::st
   return true;
 }
 
+// Words per trace at most (traces up to 16 x word_bits positions).
+constexpr int kMaxPlanes = 16;
+
 struct Layout {
   int T = 0, word_bits = 0, max_len = 0, steps = 0;
-  unsigned vecs_needed = 0;
+  int planes = 1;                // words per trace
+  unsigned plane_vecs_needed = 0;  // 16-byte vectors of one word per trace
+  unsigned vecs_needed = 0;        // all planes
 };
 
 lsyn_status validate(const lsyn_problem* p, Layout* L, std::string* err) {
@@ -251,21 +256,24 @@ lsyn_status validate(const lsyn_problem* p, Layout* L, std::string* err) {
   L->word_bits = p->word_bits;
   L->max_len = 1;
   for (int i = 0; i < L->T; ++i) {
-    if (p->lengths[i] < 1 || p->lengths[i] > p->word_bits) {
-      *err = "trace " + std::to_string(i) + " has a length outside 1..word_bits";
+    if (p->lengths[i] < 1 || p->lengths[i] > p->word_bits * kMaxPlanes) {
+      *err = "trace " + std::to_string(i) + " has a length outside 1.." + std::to_string(p->word_bits * kMaxPlanes);
       return LSYN_E_INVAL;
     }
     L->max_len = std::max(L->max_len, int(p->lengths[i]));
   }
-  L->steps = 0;
-  while ((1 << L->steps) < L->max_len) ++L->steps;
-  L->vecs_needed = unsigned((size_t(L->T) * (p->word_bits / 8) + 15) / 16);
+  L->planes = (L->max_len + p->word_bits - 1) / p->word_bits;
+  L->steps = 0;  // log-step shifts within one word
+  while ((1 << L->steps) < std::min(L->max_len, p->word_bits)) ++L->steps;
+  L->plane_vecs_needed = unsigned((size_t(L->T) * (p->word_bits / 8) + 15) / 16);
+  L->vecs_needed = L->plane_vecs_needed * unsigned(L->planes);
   return LSYN_OK;
 }
 
-// Pack the padded per-word constants and atom rows on the host.
-void pack_host(const lsyn_problem* p, const Layout& L, unsigned vecs, std::vector<uint32_t>* consts,
-               std::vector<uint32_t>* atoms) {
+// Pack the padded per-word constants and atom rows on the host: `vecs`
+// vectors per CM, plane j (a word of every trace) at vector j * plane_vecs.
+void pack_host(const lsyn_problem* p, const Layout& L, unsigned vecs, unsigned plane_vecs,
+               std::vector<uint32_t>* consts, std::vector<uint32_t>* atoms) {
   const unsigned n32 = vecs * 4;  // 32-bit words per padded CM
   consts->assign(size_t(5) * n32, 0u);
   atoms->assign(size_t(p->n_props) * n32, 0u);
@@ -286,23 +294,44 @@ void pack_host(const lsyn_problem* p, const Layout& L, unsigned vecs, std::vecto
       dst[2 * i + 1] = uint32_t(r >> 32);
     }
   };
+  const int wb = p->word_bits;
+  const unsigned words_per_plane = plane_vecs * unsigned(4 / per);  // in words of word_bits bits
   for (int i = 0; i < L.T; ++i) {
     const int len = p->lengths[i];
-    const uint64_t m = len >= 64 ? ~0ull : ((1ull << len) - 1ull);  // positions 0..len-1
-    store(lm, i, m);
-    store(lab, i, i < p->n_pos ? 1ull : 0ull);  // the position-0 bit
+    store(lab, i, i < p->n_pos ? 1ull : 0ull);  // the position-0 bit (plane 0)
     store(care, i, 1ull);
-    for (int q = 0; q < p->n_props; ++q) {
-      uint64_t w;
-      if (per == 1) w = static_cast<const uint32_t*>(p->atom_words)[size_t(q) * L.T + i];
-      else w = static_cast<const uint64_t*>(p->atom_words)[size_t(q) * L.T + i];
-      store(atoms->data() + size_t(q) * n32, i, w & m);
+    for (int j = 0; j < L.planes; ++j) {
+      // positions j*wb .. j*wb + wb - 1 of the trace, those before its end
+      const int n_in = std::max(0, std::min(wb, len - j * wb));
+      const uint64_t m = n_in >= 64 ? ~0ull : ((1ull << n_in) - 1ull);
+      const int at = int(unsigned(j) * words_per_plane) + i;
+      store(lm, at, m);
+      for (int q = 0; q < p->n_props; ++q) {
+        const size_t src = (size_t(q) * size_t(L.T) + size_t(i)) * size_t(L.planes) + size_t(j);
+        uint64_t w;
+        if (per == 1) w = static_cast<const uint32_t*>(p->atom_words)[src];
+        else w = static_cast<const uint64_t*>(p->atom_words)[src];
+        store(atoms->data() + size_t(q) * n32, at, w & m);
+      }
     }
   }
   for (unsigned i = 0; i < n32; ++i) {
     key[i] = mix32(i * 2u + 0x51ED270Bu);
     mul[i] = mix32(i * 2u + 0x2545F491u) | 1u;
   }
+}
+
+// One internal row (planes x plane_vecs vectors, position 0 in the top bit)
+// to the ABI's [trace][plane] words with bit t = position t.
+void planes_to_abi(const uint8_t* row, uint8_t* dst, int T, int planes, unsigned plane_vecs, int word_bits) {
+  const size_t wbytes = size_t(word_bits / 8);
+  const size_t words_per_plane = size_t(plane_vecs) * 16 / wbytes;
+  for (int i = 0; i < T; ++i)
+    for (int j = 0; j < planes; ++j) {
+      uint8_t* d = dst + (size_t(i) * size_t(planes) + size_t(j)) * wbytes;
+      memcpy(d, row + (size_t(j) * words_per_plane + size_t(i)) * wbytes, wbytes);
+      reverse_words(d, 1, word_bits);
+    }
 }
 
 }  // namespace
@@ -507,12 +536,20 @@ lsyn_status lsyn::ctx_shell(const lsyn_problem* problem, const lsyn_config* conf
   // Paths: A (thread per candidate) up to 128 bytes, padded to a power of two
   // of 16-byte vectors; C (one vector per lane) up to 512 bytes; D (whole
   // warps of vectors, looped per lane) up to 64 KiB.
-  unsigned vecs = 0;
-  if (L.vecs_needed <= 8 && !warp_layout) {
+  // Traces longer than a word (several planes) always take path D, each plane
+  // padded to whole warps of vectors so a lane holds the same traces' words in
+  // every plane.
+  unsigned vecs = 0, plane_vecs = 0;
+  if (L.planes == 1 && L.vecs_needed <= 8 && !warp_layout) {
     vecs = 1;
     while (vecs < L.vecs_needed) vecs <<= 1;
-  } else if (L.vecs_needed <= 4096) {
+    plane_vecs = vecs;
+  } else if (L.planes == 1 && L.vecs_needed <= 4096) {
     vecs = (L.vecs_needed + 31u) / 32u * 32u;
+    plane_vecs = vecs;
+  } else if (L.planes > 1 && (L.plane_vecs_needed + 31u) / 32u * 32u * unsigned(L.planes) <= 4096) {
+    plane_vecs = (L.plane_vecs_needed + 31u) / 32u * 32u;
+    vecs = plane_vecs * unsigned(L.planes);
   } else {
     g_create_error = "characteristic matrices above 64 KiB (" + std::to_string(L.vecs_needed * 16) +
                      " bytes) are not supported by this build";
@@ -543,6 +580,8 @@ lsyn_status lsyn::ctx_shell(const lsyn_problem* problem, const lsyn_config* conf
   c->max_len = L.max_len;
   c->steps = L.steps;
   c->vecs = vecs;
+  c->planes = unsigned(L.planes);
+  c->plane_vecs = plane_vecs;
   c->path = vecs <= 8 ? 1 : vecs == 32 ? 2 : 3;
   c->table_cap = best_cap;
   c->max_entries = unsigned(best_e);
@@ -561,7 +600,7 @@ lsyn_status lsyn::ctx_shell(const lsyn_problem* problem, const lsyn_config* conf
     g_create_error = cudaGetErrorString(e);
     return LSYN_E_CUDA;
   }
-  if (consts && atoms) pack_host(problem, L, vecs, consts, atoms);
+  if (consts && atoms) pack_host(problem, L, vecs, plane_vecs, consts, atoms);
   c->level_start.assign(1, 0);
   c->level_n.assign(1, 0);
   *out = c;
@@ -835,16 +874,28 @@ lsyn_status lsyn_level_count(const lsyn_ctx* c, int32_t k, int64_t* n_out) {
 lsyn_status lsyn_export_level(lsyn_ctx* c, int32_t k, int64_t first, int64_t count, void* dst, size_t cap) {
   if (!c || k < 1 || k > c->levels_done || first < 0 || count < 0) return LSYN_E_INVAL;
   if (uint64_t(first) + uint64_t(count) > c->level_n[k]) return c->fail(LSYN_E_INVAL, "range outside the level");
-  const size_t row = size_t(c->T) * (c->word_bits / 8);
+  const size_t wbytes = size_t(c->word_bits / 8);
+  const size_t row = size_t(c->T) * size_t(c->planes) * wbytes;
   if (count == 0) return LSYN_OK;
   if (!dst || cap < row * size_t(count)) return c->fail(LSYN_E_INVAL, "destination too small");
   cudaSetDevice(c->device);
   const uint4* src = c->arena + (size_t(c->level_start[k]) + size_t(first)) * c->vecs;
-  cudaError_t e = cudaMemcpy2DAsync(dst, row, src, size_t(c->vecs) * 16, row, size_t(count),
-                                    cudaMemcpyDeviceToHost, c->stream);
+  cudaError_t e;
+  if (c->planes == 1) {
+    e = cudaMemcpy2DAsync(dst, row, src, size_t(c->vecs) * 16, row, size_t(count), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return c->cuda_fail(e, "export");
+    reverse_words(dst, size_t(count) * size_t(c->T), c->word_bits);  // back to bit t = position t
+    return LSYN_OK;
+  }
+  // several words per trace: whole rows, then [trace][plane] words per row
+  std::vector<uint8_t> tmp(size_t(count) * size_t(c->vecs) * 16);
+  e = cudaMemcpyAsync(tmp.data(), src, tmp.size(), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return c->cuda_fail(e, "export");
-  reverse_words(dst, size_t(count) * size_t(c->T), c->word_bits);  // back to bit t = position t
+  for (int64_t r = 0; r < count; ++r)
+    planes_to_abi(tmp.data() + size_t(r) * c->vecs * 16, static_cast<uint8_t*>(dst) + size_t(r) * row, c->T,
+                  int(c->planes), c->plane_vecs, c->word_bits);
   return LSYN_OK;
 }
 
@@ -868,10 +919,11 @@ lsyn_status lsyn_eval(const lsyn_problem* problem, const char* formula, void* ds
   if (config) cfg = *config;
   if (cfg.device >= 0 && cudaSetDevice(cfg.device) != cudaSuccess) { g_create_error = "bad device"; return LSYN_E_CUDA; }
   cudaStream_t stream = static_cast<cudaStream_t>(cfg.stream);
-  const unsigned vecs = std::max(1u, L.vecs_needed);
+  const unsigned plane_vecs = std::max(1u, L.plane_vecs_needed);
+  const unsigned vecs = plane_vecs * unsigned(L.planes);
   const size_t M = size_t(vecs) * 16;
   std::vector<uint32_t> consts, atoms;
-  pack_host(problem, L, vecs, &consts, &atoms);
+  pack_host(problem, L, vecs, plane_vecs, &consts, &atoms);
   Alloc mem;
   mem.alloc = cfg.alloc;
   mem.free = cfg.free;
@@ -894,10 +946,10 @@ lsyn_status lsyn_eval(const lsyn_problem* problem, const char* formula, void* ds
     e = cudaMemcpyAsync(d_nodes, nodes.data(), nodes.size() * sizeof(int4), cudaMemcpyHostToDevice, stream);
   if (e == cudaSuccess) {
     if (L.word_bits == 32)
-      e = Kernels<uint32_t>::eval(d_atoms, d_lm, vecs, d_nodes, int(nodes.size()), L.steps,
+      e = Kernels<uint32_t>::eval(d_atoms, d_lm, plane_vecs, unsigned(L.planes), d_nodes, int(nodes.size()), L.steps,
                                   reinterpret_cast<uint32_t*>(d_scratch), reinterpret_cast<uint32_t*>(d_out), lc);
     else
-      e = Kernels<uint64_t>::eval(d_atoms, d_lm, vecs, d_nodes, int(nodes.size()), L.steps,
+      e = Kernels<uint64_t>::eval(d_atoms, d_lm, plane_vecs, unsigned(L.planes), d_nodes, int(nodes.size()), L.steps,
                                   reinterpret_cast<uint64_t*>(d_scratch), reinterpret_cast<uint64_t*>(d_out), lc);
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(host_out.data(), d_out, M, cudaMemcpyDeviceToHost, stream);
@@ -907,8 +959,8 @@ lsyn_status lsyn_eval(const lsyn_problem* problem, const char* formula, void* ds
     g_create_error = std::string("eval: ") + cudaGetErrorString(e);
     return LSYN_E_CUDA;
   }
-  reverse_words(host_out.data(), size_t(L.T), L.word_bits);  // back to bit t = position t
-  memcpy(dst, host_out.data(), size_t(L.T) * (L.word_bits / 8));
+  // back to the ABI's [trace][plane] words with bit t = position t
+  planes_to_abi(host_out.data(), static_cast<uint8_t*>(dst), L.T, L.planes, plane_vecs, L.word_bits);
   return LSYN_OK;
 }
 

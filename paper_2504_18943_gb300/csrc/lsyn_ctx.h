@@ -109,6 +109,7 @@ struct lsyn_ctx {
   // problem
   int n_props = 0, n_pos = 0, n_neg = 0, T = 0, word_bits = 32, max_len = 1, steps = 0;
   unsigned vecs = 0;
+  unsigned planes = 1, plane_vecs = 0;  // words per trace, vectors per plane
   int path = 0;
   int sms = 1;
   // device memory
@@ -179,6 +180,8 @@ struct lsyn_ctx {
     cv.chunk = chunk;
     cv.steps = steps;
     cv.early_exit = full_levels ? 0 : 1;
+    cv.planes = planes;
+    cv.plane_vecs = plane_vecs;
     return cv;
   }
 };

@@ -5,11 +5,12 @@
 // with LSYN_WORD defined.
 //
 // Layout. A characteristic matrix (CM) is one word per trace, positives first,
-// padded with zero words to `vecs` 16-byte vectors. Bit t of a trace word says
-// whether the formula holds at position t ("Parallel enumeration of LTLf
-// formulae on GPUs": characteristic sequence, least significant bit = position
-// 0). Padding bits (positions >= length, padding traces) are zero for every
-// formula.
+// padded with zero words to `vecs` 16-byte vectors; a word holds a trace's
+// characteristic sequence ("Parallel enumeration of LTLf formulae on GPUs"),
+// position 0 in the most significant bit. Traces longer than a word take one
+// word per "plane": plane j holds positions [j w, (j + 1) w) of every trace and
+// occupies `plane_vecs` vectors. Padding bits (positions >= length, padding
+// traces) are zero for every formula.
 #pragma once
 
 #include <algorithm>
@@ -75,6 +76,118 @@ __device__ __forceinline__ W w_op(uint32_t op, W a, W b, W lm, int /*steps*/) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Traces longer than a word (planes). The operators carry one word of
+// information from the later planes of the same trace:
+//   X: the last position of plane j takes the first position of plane j + 1;
+//   F: every position of plane j holds if any later plane has a set bit;
+//   U: U at the first position of plane j + 1 enters plane j's adder as a
+//      carry-in (a psi just after the word's last position), so U is computed
+//      from the last plane to the first.
+// Positions past a trace's end are 0 in every plane, so no carry crosses it.
+// ---------------------------------------------------------------------------
+template <typename W>
+__device__ __forceinline__ W w_top(W a) {  // the position-0 bit as 0 / 1
+  return a >> (sizeof(W) * 8 - 1);
+}
+
+template <typename W>
+__device__ __forceinline__ W w_until_cin(W phi, W psi, W cin) {
+  const W c = ((phi | psi) + psi + cin) ^ (phi & ~psi);
+  return psi | (phi & c);
+}
+
+// The words of one 16-byte vector.
+template <typename W>
+struct Words;
+template <>
+struct Words<uint32_t> {
+  static constexpr int N = 4;
+  uint32_t w[4];
+  __device__ static Words load(uint4 v) { return Words{{v.x, v.y, v.z, v.w}}; }
+  __device__ uint4 store() const { return make_uint4(w[0], w[1], w[2], w[3]); }
+};
+template <>
+struct Words<uint64_t> {
+  static constexpr int N = 2;
+  uint64_t w[2];
+  __device__ static Words load(uint4 v) {
+    return Words{{uint64_t(v.x) | (uint64_t(v.y) << 32), uint64_t(v.z) | (uint64_t(v.w) << 32)}};
+  }
+  __device__ uint4 store() const {
+    return make_uint4(uint32_t(w[0]), uint32_t(w[0] >> 32), uint32_t(w[1]), uint32_t(w[1] >> 32));
+  }
+};
+
+// Vector u of plane j of op(a, b) on multi-plane rows: A(k), B(k), LM(k) give
+// vector u of plane k of the operands and of the length masks.
+template <typename W, class FA, class FB, class FL>
+__device__ uint4 mp_op(uint32_t op, unsigned j, unsigned planes, const FA& A, const FB& B, const FL& LM) {
+  using V = Words<W>;
+  switch (op) {
+    case kNot: {
+      V a = V::load(A(j));
+      const V m = V::load(LM(j));
+#pragma unroll
+      for (int i = 0; i < V::N; ++i) a.w[i] = ~a.w[i] & m.w[i];
+      return a.store();
+    }
+    case kAnd: {
+      const uint4 a = A(j), b = B(j);
+      return make_uint4(a.x & b.x, a.y & b.y, a.z & b.z, a.w & b.w);
+    }
+    case kOr: {
+      const uint4 a = A(j), b = B(j);
+      return make_uint4(a.x | b.x, a.y | b.y, a.z | b.z, a.w | b.w);
+    }
+    case kNext: {
+      V a = V::load(A(j));
+      const V n = j + 1 < planes ? V::load(A(j + 1)) : V::load(make_uint4(0, 0, 0, 0));
+#pragma unroll
+      for (int i = 0; i < V::N; ++i) a.w[i] = (a.w[i] << 1) | w_top<W>(n.w[i]);
+      return a.store();
+    }
+    case kFuture:
+    case kGlobally: {
+      const bool g = op == kGlobally;  // G = not F not, negation masked to the trace
+      V later = V::load(make_uint4(0, 0, 0, 0));
+      for (int k = int(planes) - 1; k > int(j); --k) {
+        V x = V::load(A(unsigned(k)));
+        if (g) {
+          const V m = V::load(LM(unsigned(k)));
+#pragma unroll
+          for (int i = 0; i < V::N; ++i) x.w[i] = ~x.w[i] & m.w[i];
+        }
+#pragma unroll
+        for (int i = 0; i < V::N; ++i) later.w[i] |= x.w[i];
+      }
+      V x = V::load(A(j));
+      const V m = V::load(LM(j));
+#pragma unroll
+      for (int i = 0; i < V::N; ++i) {
+        const W xi = g ? (~x.w[i] & m.w[i]) : x.w[i];
+        const W f = w_future<W>(xi) | (later.w[i] ? m.w[i] : W(0));
+        x.w[i] = g ? (~f & m.w[i]) : f;
+      }
+      return x.store();
+    }
+    case kUntil: {
+      V c = V::load(make_uint4(0, 0, 0, 0)), r = c;
+      for (int k = int(planes) - 1; k >= int(j); --k) {
+        const V phi = V::load(A(unsigned(k))), psi = V::load(B(unsigned(k)));
+#pragma unroll
+        for (int i = 0; i < V::N; ++i) {
+          r.w[i] = w_until_cin<W>(phi.w[i], psi.w[i], c.w[i]);
+          c.w[i] = w_top<W>(r.w[i]);
+        }
+      }
+      return r.store();
+    }
+    default:
+      return make_uint4(0, 0, 0, 0);
+  }
+}
+
 // `steps` is the smallest s with 2^s >= the longest trace.
 template <typename W>
 __device__ __forceinline__ W w_future_logstep(W a, int steps) {
@@ -133,6 +246,18 @@ __device__ __forceinline__ uint4 v_op<uint64_t>(uint32_t op, uint4 a, uint4 b, u
   return make4(w_op<uint64_t>(op, lo64(a), lo64(b), lo64(lm), steps),
                w_op<uint64_t>(op, hi64(a), hi64(b), hi64(lm), steps));
 }
+
+// Vector v of op(row a, row b) of a CM in global memory, planes or not.
+template <typename W>
+__device__ __forceinline__ uint4 row_op(const CacheView& cv, uint32_t op, const uint4* a, const uint4* b, unsigned v) {
+  if (cv.planes <= 1) return v_op<W>(op, __ldg(a + v), __ldg(b + v), __ldg(cv.lenmask + v), 0);
+  const unsigned pv = cv.plane_vecs, j = v / pv, u = v - j * pv;
+  if (j >= cv.planes) return make_uint4(0, 0, 0, 0);  // padding vectors after the last plane
+  return mp_op<W>(op, j, cv.planes, [&](unsigned k) { return __ldg(a + k * pv + u); },
+                  [&](unsigned k) { return __ldg(b + k * pv + u); },
+                  [&](unsigned k) { return __ldg(cv.lenmask + k * pv + u); });
+}
+
 
 // ---------------------------------------------------------------------------
 // Hash of a CM: over its 32-bit words w_i, H = (sum hi32(p_i), sum lo32(p_i))
@@ -920,7 +1045,7 @@ struct PathD {
         const unsigned v = lane + 32u * r;
         const uint4 c = gen.compute(q, v);
         acc = h_mac(c, __ldg(cv.hmul + v), acc);
-        diff |= bit0s<W>(c) ^ bit0s<W>(__ldg(cv.label + v));
+        if (v < cv.plane_vecs) diff |= bit0s<W>(c) ^ bit0s<W>(__ldg(cv.label + v));  // position 0: plane 0
       }
       const uint32_t lo = __reduce_add_sync(kFull, uint32_t(acc));
       const uint32_t hi = __reduce_add_sync(kFull, uint32_t(acc >> 32));
@@ -1043,12 +1168,13 @@ struct PairGenD {
   const uint2* pairs;  // shared memory: (a id, b id) of pair p
   __device__ uint4 compute(int q, unsigned v) const {
     const uint2 pr = pairs[q >> 2];
-    const uint4 a = __ldg(row_ptr(*cv, pr.x) + v), b = __ldg(row_ptr(*cv, pr.y) + v);
+    const uint4* a = row_ptr(*cv, pr.x);
+    const uint4* b = row_ptr(*cv, pr.y);
     switch (q & 3) {
-      case 0: return v_op<W>(kAnd, a, b, b, 0);
-      case 1: return v_op<W>(kOr, a, b, b, 0);
-      case 2: return v_op<W>(kUntil, a, b, b, 0);
-      default: return v_op<W>(kUntil, b, a, b, 0);
+      case 0: return row_op<W>(*cv, kAnd, a, b, v);
+      case 1: return row_op<W>(*cv, kOr, a, b, v);
+      case 2: return row_op<W>(*cv, kUntil, a, b, v);
+      default: return row_op<W>(*cv, kUntil, b, a, v);
     }
   }
   __device__ uint64_t desc(int q) const {
@@ -1067,8 +1193,8 @@ struct RowGenD {
   const CacheView* cv;
   uint32_t id0;
   __device__ uint4 compute(int q, unsigned v) const {
-    const uint4 a = __ldg(row_ptr(*cv, id0 + uint32_t(q >> 2)) + v);
-    return v_op<W>(unary_code(q & 3), a, a, __ldg(cv->lenmask + v), 0);
+    const uint4* a = row_ptr(*cv, id0 + uint32_t(q >> 2));
+    return row_op<W>(*cv, unary_code(q & 3), a, a, v);
   }
   __device__ uint64_t desc(int q) const { return pack_desc(unary_code(q & 3), id0 + uint32_t(q >> 2), 0); }
 };
@@ -1081,9 +1207,9 @@ struct ListGenD {
     const uint64_t dd = d[q];
     const uint32_t op = desc_op(dd);
     if (op == kAtom) return __ldg(cv->atoms + size_t(desc_left(dd)) * cv->vecs + v);
-    const uint4 a = __ldg(row_ptr(*cv, desc_left(dd)) + v);
-    const uint4 b = (op == kAnd || op == kOr || op == kUntil) ? __ldg(row_ptr(*cv, desc_right(dd)) + v) : a;
-    return v_op<W>(op, a, b, __ldg(cv->lenmask + v), 0);
+    const uint4* a = row_ptr(*cv, desc_left(dd));
+    const uint4* b = (op == kAnd || op == kOr || op == kUntil) ? row_ptr(*cv, desc_right(dd)) : a;
+    return row_op<W>(*cv, op, a, b, v);
   }
   __device__ uint64_t desc(int q) const { return d[q]; }
 };
@@ -1519,23 +1645,56 @@ static __global__ void __launch_bounds__(256) k_rehash(const unsigned long long*
 // w = proposition); scratch holds one row of words per node.
 // ===========================================================================
 template <typename W>
-__global__ void k_eval(const W* atoms, const W* lenmask, unsigned words, const int4* nodes, int n_nodes, int steps,
-                       W* scratch, W* out) {
-  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_eval(const W* atoms, const W* lenmask, unsigned words, unsigned planes, const int4* nodes,
+                       int n_nodes, int steps, W* scratch, W* out) {
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;  // word slot of a plane (a trace)
   if (t >= words) return;
-  const W lm = lenmask[t];
+  const size_t row = size_t(words) * planes;  // one CM: planes x words
+  constexpr int kBits = int(sizeof(W) * 8);
   for (int i = 0; i < n_nodes; ++i) {
     const int4 nd = nodes[i];
-    W v;
-    if (nd.x == int(kAtom)) v = atoms[size_t(nd.w) * words + t];
-    else {
-      const W a = scratch[size_t(nd.y) * words + t];
-      const W b = nd.z >= 0 ? scratch[size_t(nd.z) * words + t] : a;
-      v = w_op_logstep<W>(uint32_t(nd.x), a, b, lm, steps);
+    const uint32_t op = uint32_t(nd.x);
+    W* dst = scratch + size_t(i) * row;
+    if (op == kAtom) {
+      for (unsigned j = 0; j < planes; ++j) dst[j * words + t] = atoms[size_t(nd.w) * row + j * words + t];
+      continue;
     }
-    scratch[size_t(i) * words + t] = v;
+    const W* a = scratch + size_t(nd.y) * row;
+    const W* b = nd.z >= 0 ? scratch + size_t(nd.z) * row : a;
+    // planes from the last: later positions carry into earlier words
+    W later = 0, cin = 0;
+    for (int j = int(planes) - 1; j >= 0; --j) {
+      const size_t o = size_t(j) * words + t;
+      const W lm = lenmask[o];
+      W v;
+      switch (op) {
+        case kNext:
+          v = (a[o] << 1) | (size_t(j) + 1 < planes ? (a[o + words] >> (kBits - 1)) : W(0));
+          break;
+        case kFuture:
+          v = w_future_logstep<W>(a[o], steps) | (later ? lm : W(0));
+          later |= a[o];
+          break;
+        case kGlobally: {
+          const W na = ~a[o] & lm;
+          v = ~(w_future_logstep<W>(na, steps) | (later ? lm : W(0))) & lm;
+          later |= na;
+          break;
+        }
+        case kUntil: {
+          // within the word, or phi to the word's end and U where the next word starts
+          const W phi_to_end = ~w_future_logstep<W>(~a[o], steps);
+          v = w_until_logstep<W>(a[o], b[o], steps) | (cin ? phi_to_end : W(0));
+          cin = v >> (kBits - 1);
+          break;
+        }
+        default:
+          v = w_op_logstep<W>(op, a[o], b[o], lm, steps);
+      }
+      dst[o] = v;
+    }
   }
-  out[t] = scratch[size_t(n_nodes - 1) * words + t];
+  for (unsigned j = 0; j < planes; ++j) out[j * words + t] = scratch[size_t(n_nodes - 1) * row + j * words + t];
 }
 
 // ===========================================================================
@@ -1704,12 +1863,12 @@ cudaError_t Kernels<W>::fixup(const CacheView& cv, const uint2* moves, unsigned 
 }
 
 template <typename W>
-cudaError_t Kernels<W>::eval(const uint4* atoms, const uint4* lenmask, unsigned vecs, const int4* nodes,
-                             int n_nodes, int steps, W* scratch, W* out, const LaunchCfg& lc) {
-  const unsigned words = vecs * unsigned(sizeof(uint4) / sizeof(W));
+cudaError_t Kernels<W>::eval(const uint4* atoms, const uint4* lenmask, unsigned plane_vecs, unsigned planes,
+                             const int4* nodes, int n_nodes, int steps, W* scratch, W* out, const LaunchCfg& lc) {
+  const unsigned words = plane_vecs * unsigned(sizeof(uint4) / sizeof(W));
   k_eval<W><<<(words + 127u) / 128u, 128, 0, lc.stream>>>(reinterpret_cast<const W*>(atoms),
-                                                          reinterpret_cast<const W*>(lenmask), words, nodes,
-                                                          n_nodes, steps, scratch, out);
+                                                          reinterpret_cast<const W*>(lenmask), words, planes,
+                                                          nodes, n_nodes, steps, scratch, out);
   return cudaGetLastError();
 }
 

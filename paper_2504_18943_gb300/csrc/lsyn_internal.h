@@ -77,8 +77,10 @@ struct CacheView {
   uint2* holes;                  // [hole_cap]: unused id ranges [x, y) left by warps
   unsigned int hole_cap;
   unsigned int chunk;            // ids a warp reserves per counter update (path B)
-  int steps;                     // log-step count: 2^steps >= longest trace
+  int steps;                     // log-step count: 2^steps >= longest trace (at most the word width)
   int early_exit;                // 1: stop at the first separating candidate
+  unsigned int planes;           // words per trace: plane j holds positions [j w, (j + 1) w) of every trace
+  unsigned int plane_vecs;       // vectors of one plane (vecs = planes x plane_vecs, then padding)
 };
 
 // One split {i, j} of level k (i + j = k - 1) for the binary operators.
@@ -161,10 +163,10 @@ struct Kernels {
                             unsigned* error, const LaunchCfg& lc);
   // Move entries src -> dst (pairs), repointing their table slots.
   static cudaError_t fixup(const CacheView& cv, const uint2* moves, unsigned n, const LaunchCfg& lc);
-  // Evaluate a postorder node list on every trace word: scratch [n_nodes][words].
-  static cudaError_t eval(const uint4* atoms, const uint4* lenmask, unsigned vecs,
-                          const int4* nodes, int n_nodes, int steps, W* scratch, W* out,
-                          const LaunchCfg& lc);
+  // Evaluate a postorder node list on every trace word of every plane:
+  // scratch [n_nodes][planes][plane words]; a CM of planes x plane_vecs vectors.
+  static cudaError_t eval(const uint4* atoms, const uint4* lenmask, unsigned plane_vecs, unsigned planes,
+                          const int4* nodes, int n_nodes, int steps, W* scratch, W* out, const LaunchCfg& lc);
 };
 
 }  // namespace lsyn

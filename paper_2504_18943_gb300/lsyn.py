@@ -215,7 +215,8 @@ def _check(status: int, ctx=None, ok=(LSYN_OK,)) -> int:
 # ---------------------------------------------------------------------------
 
 class PackedProblem:
-    """A problem in the ABI layout: atom words [n_props][T] and lengths [T].
+    """A problem in the ABI layout: atom words [n_props][T] (one word per trace)
+    or [n_props][T][W] (W words per trace) and lengths [T].
 
     Holds the numpy buffers the ``lsyn_problem`` struct points to."""
 
@@ -234,6 +235,11 @@ class PackedProblem:
         return self.n_pos + self.n_neg
 
     @property
+    def planes(self) -> int:
+        """Words per trace."""
+        return int(self.atom_words.shape[2]) if self.atom_words.ndim == 3 else 1
+
+    @property
     def word_dtype(self):
         return np.uint32 if self.word_bits == 32 else np.uint64
 
@@ -243,16 +249,26 @@ class PackedProblem:
 
 
 def pack_traces(bits: np.ndarray, lengths: np.ndarray, n_pos: int, n_neg: int, word_bits: int) -> PackedProblem:
-    """Pack boolean traces ``bits[i, t, p]`` into atom words (bit t of word (p, i))."""
+    """Pack boolean traces ``bits[i, t, p]`` into atom words: bit t of word
+    (p, i) when every trace fits a word, else bit t of word (p, i, w) for
+    position w * word_bits + t (W = ceil(longest / word_bits) words)."""
     bits = np.asarray(bits, dtype=bool)
     T, L, n = bits.shape
-    if L > word_bits:
-        if bits[:, word_bits:, :].any():
-            raise ValueError("a trace is longer than the word width")
-        bits = bits[:, :word_bits, :]
-        L = word_bits
-    weights = np.left_shift(np.uint64(1), np.arange(L, dtype=np.uint64))
-    words = (bits.transpose(2, 0, 1).astype(np.uint64) * weights[None, None, :]).sum(axis=2, dtype=np.uint64)
+    longest = int(np.max(lengths)) if len(lengths) else 1
+    planes = max(1, -(-longest // word_bits))
+    if L > planes * word_bits:
+        if bits[:, planes * word_bits:, :].any():
+            raise ValueError("a trace has propositions past its length")
+        bits = bits[:, :planes * word_bits, :]
+        L = planes * word_bits
+    if L < planes * word_bits:
+        bits = np.concatenate([bits, np.zeros((T, planes * word_bits - L, n), dtype=bool)], axis=1)
+    weights = np.left_shift(np.uint64(1), np.arange(word_bits, dtype=np.uint64))
+    # [n][T][planes][word_bits] -> words
+    b = bits.transpose(2, 0, 1).reshape(n, T, planes, word_bits).astype(np.uint64)
+    words = (b * weights[None, None, None, :]).sum(axis=3, dtype=np.uint64)
+    if planes == 1:
+        words = words[:, :, 0]
     return PackedProblem(n, n_pos, n_neg, word_bits, lengths, words)
 
 
@@ -375,12 +391,13 @@ def lsyn_level_count(ctx, k: int) -> int:
 
 
 def lsyn_export_level(ctx, k: int, n_traces: int, word_bits: int, first: int = 0,
-                      count: Optional[int] = None) -> np.ndarray:
-    """CMs of level k as an array [count, n_traces] of uint32/uint64 words."""
+                      count: Optional[int] = None, planes: int = 1) -> np.ndarray:
+    """CMs of level k as an array [count, n_traces] (or [count, n_traces, planes]
+    with several words per trace) of uint32/uint64 words."""
     if count is None:
         count = lsyn_level_count(ctx, k) - first
     dt = np.uint32 if word_bits == 32 else np.uint64
-    out = np.empty((count, n_traces), dtype=dt)
+    out = np.empty((count, n_traces) if planes == 1 else (count, n_traces, planes), dtype=dt)
     _check(_lib.lsyn_export_level(ctx, k, first, count, out.ctypes.data if count else None, out.nbytes), ctx)
     return out
 
@@ -392,7 +409,9 @@ def lsyn_entry_formula(ctx, k: int, index: int, cap: int = 1 << 16) -> str:
 
 
 def lsyn_eval(problem: PackedProblem, formula: str, config: Optional[lsyn_config] = None) -> np.ndarray:
-    out = np.zeros(problem.n_traces, dtype=problem.word_dtype)
+    """The formula's CM: [n_traces] words, or [n_traces, planes] with several words per trace."""
+    shape = problem.n_traces if problem.planes == 1 else (problem.n_traces, problem.planes)
+    out = np.zeros(shape, dtype=problem.word_dtype)
     st = _lib.lsyn_eval(ctypes.byref(problem.struct), formula.encode(), out.ctypes.data,
                         ctypes.byref(config) if config is not None else None)
     _check(st, None)
@@ -421,8 +440,8 @@ def lsyn_level_candidates(level_sizes: Sequence[int], k: int, op_mask: int = OPS
 def labeller(formula: str, traces, n_props: int) -> np.ndarray:
     """Workload labeller on the GPU: True where trace, 0 |= formula (lsyn_eval)."""
     p = pack_traces(traces.bits, traces.lengths, len(traces.lengths), 0, 64)
-    cm = lsyn_eval(p, formula)
-    return (cm & np.uint64(1)).astype(bool)
+    cm = lsyn_eval(p, formula).reshape(p.n_traces, -1)
+    return (cm[:, 0] & np.uint64(1)).astype(bool)  # position 0: bit 0 of a trace's first word
 
 
 def cm_strings(words: np.ndarray, lengths: Sequence[int]) -> str:
@@ -472,7 +491,8 @@ class Synthesizer:
         return lsyn_level_count(self.ctx, k)
 
     def export(self, k: int, first: int = 0, count: Optional[int] = None) -> np.ndarray:
-        return lsyn_export_level(self.ctx, k, self.problem.n_traces, self.problem.word_bits, first, count)
+        return lsyn_export_level(self.ctx, k, self.problem.n_traces, self.problem.word_bits, first, count,
+                                 self.problem.planes)
 
     def formula(self, k: int, index: int) -> str:
         return lsyn_entry_formula(self.ctx, k, index)
@@ -589,7 +609,7 @@ class Batch:
 
     def export(self, i: int, k: int) -> np.ndarray:
         p = self.problems[i]
-        return lsyn_export_level(lsyn_batch_problem(self.handle, i), k, p.n_traces, p.word_bits)
+        return lsyn_export_level(lsyn_batch_problem(self.handle, i), k, p.n_traces, p.word_bits, planes=p.planes)
 
     def stats(self) -> dict:
         return lsyn_batch_stats(self.handle)

@@ -207,8 +207,8 @@ def labelled_problem(name: str, seed: int, n_props: int, n_pos: int, n_neg: int,
     formula is redrawn. Per-proposition probabilities are uniform in
     [prob_lo, prob_hi] (a constant when the two are equal).
     """
-    if len_hi > word_bits:
-        raise ValueError("traces longer than the word width")
+    if len_hi > 16 * word_bits:
+        raise ValueError("traces longer than 16 words")
     cap = 10 ** 4 + 40 * (n_pos + n_neg)
     for attempt in range(max_attempts):
         fst = Stream(stream_key(seed, 1, attempt))

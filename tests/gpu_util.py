@@ -18,15 +18,26 @@ def lib():
     return lsyn
 
 
-def oracle_rows(cms, word_bits: int, n_traces: int) -> np.ndarray:
-    """Oracle CM strings ('0'/'1', position 0 first, traces joined by ',') as words."""
+def oracle_rows(cms, word_bits: int, n_traces: int, planes: int = 1) -> np.ndarray:
+    """Oracle CM strings ('0'/'1', position 0 first, traces joined by ',') as
+    words: [rows, traces], or [rows, traces, planes] with word w of a trace
+    holding positions w * word_bits + t in bit t."""
     dt = np.uint32 if word_bits == 32 else np.uint64
-    out = np.zeros((len(cms), n_traces), dtype=dt)
+    mask = (1 << word_bits) - 1
+    out = np.zeros((len(cms), n_traces, planes), dtype=dt)
     for r, cm in enumerate(cms):
         seqs = cm.split(",")
         assert len(seqs) == n_traces
-        out[r] = [int(s[::-1], 2) if s else 0 for s in seqs]
-    return out
+        for i, s in enumerate(seqs):
+            v = int(s[::-1], 2) if s else 0
+            for w in range(planes):
+                out[r, i, w] = (v >> (w * word_bits)) & mask
+    return out[:, :, 0] if planes == 1 else out
+
+
+def planes_of(problem) -> int:
+    """Words per trace of a workloads.Problem."""
+    return max(1, -(-int(np.max(problem.traces.lengths)) // problem.word_bits))
 
 
 def canon(rows: np.ndarray) -> np.ndarray:
@@ -51,7 +62,7 @@ def assert_levels_match(L, problem, depth, op_mask=0x7F, cache_bytes=256 << 20, 
             assert rows.shape[0] == run.size(k), (k, rows.shape[0], run.size(k))
             got = canon(rows)
             assert got.shape[0] == rows.shape[0], f"duplicate CMs inside level {k}"
-            want = canon(oracle_rows(run.cms(k), problem.word_bits, problem.n_traces))
+            want = canon(oracle_rows(run.cms(k), problem.word_bits, problem.n_traces, planes_of(problem)))
             assert np.array_equal(got, want), f"level {k} differs from the oracle"
             seen.append(rows)
         allrows = np.concatenate(seen) if seen else np.zeros((0, problem.n_traces))
@@ -61,7 +72,7 @@ def assert_levels_match(L, problem, depth, op_mask=0x7F, cache_bytes=256 << 20, 
             n = s.count(k)
             for idx in sorted(set([0, n // 2, n - 1])) if n else []:
                 f = s.formula(k, idx)
-                cm = oracle_rows([spec.eval(f)], problem.word_bits, problem.n_traces)[0]
+                cm = oracle_rows([spec.eval(f)], problem.word_bits, problem.n_traces, planes_of(problem))[0]
                 assert np.array_equal(cm, s.export(k, idx, 1)[0]), (k, idx, f)
                 from paper_2504_18943_gb300.workloads import formula_size
                 assert formula_size(f) == k, (k, f)

@@ -90,7 +90,7 @@ def test_create_rejects_bad_problems_before_touching_a_gpu(L, bad):
     elif bad == "word_bits":
         wb = 16
     elif bad == "length":
-        lengths[1] = 40
+        lengths[1] = 16 * 32 + 1  # more than 16 words
     elif bad == "empty":
         n_pos = n_neg = 0
     p = L.PackedProblem(n_props, n_pos, n_neg, 32, lengths, words)
