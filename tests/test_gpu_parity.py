@@ -336,3 +336,14 @@ def test_large_workload_full_size(L):
                 f_k = s.formula(k, int(idx))
                 cm = oracle_rows([spec.eval(f_k)], 64, p.n_traces)[0]
                 assert np.array_equal(cm, s.export(k, int(idx), 1)[0]) and W.formula_size(f_k) == k
+
+
+@pytest.mark.parametrize("word_bits,n_traces", [(32, 40), (32, 100), (64, 44), (32, 140), (64, 90), (64, 130)])
+def test_levels_odd_trace_counts(L, word_bits, n_traces):
+    """Trace counts that are not a multiple of the CM's vector width (10 to 65
+    vectors of real traces, padded to the kernel path's row width); levels
+    equal the oracle's."""
+    half = n_traces // 2
+    p = W.labelled_problem("odd", 7 + n_traces, 3, half, n_traces - half, 4, min(word_bits, 24), 5, word_bits,
+                           oracle.labeller)
+    assert_levels_match(L, p, 5, cache_bytes=512 << 20)
