@@ -632,10 +632,11 @@ lsyn_status lsyn::ctx_create(const lsyn_problem* problem, const lsyn_config* con
   c->homes = static_cast<unsigned*>(c->mem.get(size_t(c->max_entries) * 4));
   c->holes = static_cast<uint2*>(c->mem.get(size_t(c->hole_cap) * sizeof(uint2)));
   c->moves = static_cast<uint2*>(c->mem.get(size_t(c->move_cap) * sizeof(uint2)));
+  c->hole_bits = static_cast<unsigned*>(c->mem.get((3 * size_t(c->hole_cap) + 32) * sizeof(unsigned)));
   c->fbuf = static_cast<char*>(c->mem.get(lsyn_ctx::kFormulaCap));
   c->fstatus = static_cast<int*>(c->mem.get(sizeof(int)));
   if (!c->arena || !c->prov || !c->table || !c->ctr || !c->consts || !c->atoms || !c->defer[0] || !c->defer[1] ||
-      !c->fbuf || !c->fstatus || !c->slotpos || !c->homes || !c->holes || !c->moves)
+      !c->fbuf || !c->fstatus || !c->slotpos || !c->homes || !c->holes || !c->moves || !c->hole_bits)
     return bail(LSYN_E_NOMEM, "device allocation failed");
   if (cudaMallocHost(&c->h_snap, sizeof(Snap) * lsyn_ctx::kSnaps) != cudaSuccess ||
       cudaMallocHost(&c->h_fbuf, lsyn_ctx::kFormulaCap) != cudaSuccess ||
@@ -741,64 +742,64 @@ lsyn_status lsyn_enumerate_level(lsyn_ctx* c, int32_t k, lsyn_level_stats* out) 
       binary_snap = snap - 1;
     }
   }
-  if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return c->cuda_fail(e, "level sync");
-
-  // Deferred candidates: re-examine them until none is left (ping-pong lists).
-  unsigned long long deferred = 0;
-  int cur = 0;
-  for (int pass = 0;; ++pass) {
-    const DevCounters& h = c->h_snap[snap - 1].c;
-    if (h.defer_overflow) return c->fail(LSYN_E_STATE, "deferred list overflow: the level is not exact");
-    if (h.error) return c->fail(LSYN_E_STATE, "hash table probe overflow");
-    const unsigned n = std::min(h.defer_n[cur], c->defer_cap);
-    if (n == 0) break;
-    if (pass >= 48) return c->fail(LSYN_E_STATE, "deferred candidates did not settle");
-    deferred += n;
-    if ((e = cudaMemsetAsync(&c->ctr->defer_n[1 - cur], 0, sizeof(unsigned), c->stream)) != cudaSuccess)
+  // Close the level without a host round trip in the common case: one pass
+  // over the deferred candidates (its count is read on the device) and the
+  // hole plan + moves are queued behind the level's kernels, then read back
+  // with one synchronisation. Candidates deferred again by that pass (rare)
+  // are settled by host-driven passes, then the holes they left are closed.
+  const int main_snap = snap - 1;
+  auto pass = [&](int from, unsigned n) -> lsyn_status {  // re-examine list `from` into list 1 - from
+    if ((e = cudaMemsetAsync(&c->ctr->defer_n[1 - from], 0, sizeof(unsigned), c->stream)) != cudaSuccess)
       return c->cuda_fail(e, "memset");
-    CacheView rv = c->view(c->defer[1 - cur], &c->ctr->defer_n[1 - cur]);
+    CacheView rv = c->view(c->defer[1 - from], &c->ctr->defer_n[1 - from]);
     rv.early_exit = 0;  // a deferred candidate must be settled even after a solution
     ev_begin();
-    lsyn_status s = launch_desc(c, rv, c->defer[cur], &c->ctr->defer_n[cur], n, 0, lc);
+    lsyn_status s = launch_desc(c, rv, c->defer[from], &c->ctr->defer_n[from], n, 0, lc);
     ++launches;
     if (s != LSYN_OK) return s;
     ev_end(2);
+    return LSYN_OK;
+  };
+  auto close_holes = [&]() -> lsyn_status {
+    ev_begin();
+    e = c->word_bits == 32 ? Kernels<uint32_t>::close_holes(cv, start, c->hole_bits, c->moves, c->move_cap, lc)
+                           : Kernels<uint64_t>::close_holes(cv, start, c->hole_bits, c->moves, c->move_cap, lc);
+    launches += 3;
+    if (e != cudaSuccess) return c->cuda_fail(e, "hole fixup kernels");
+    ev_end(3);
+    if ((e = take_snap()) != cudaSuccess) return c->cuda_fail(e, "snapshot");
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return c->cuda_fail(e, "level sync");
+    return LSYN_OK;
+  };
+  lsyn_status ls = pass(0, c->defer_cap);
+  if (ls != LSYN_OK) return ls;
+  if ((e = take_snap()) != cudaSuccess) return c->cuda_fail(e, "snapshot");
+  if ((ls = close_holes()) != LSYN_OK) return ls;
+  unsigned long long deferred = std::min(c->h_snap[main_snap].c.defer_n[0], c->defer_cap);
+  int cur = 1;
+  for (int npass = 1;; ++npass) {
+    const DevCounters& h = c->h_snap[snap - 1].c;
+    if (h.defer_overflow) return c->fail(LSYN_E_STATE, "deferred list overflow: the level is not exact");
+    if (h.error == 1) return c->fail(LSYN_E_STATE, "hash table probe overflow");
+    if (h.error) break;  // reported below
+    const unsigned n = std::min(h.defer_n[cur], c->defer_cap);
+    if (n == 0) break;
+    if (npass >= 48) return c->fail(LSYN_E_STATE, "deferred candidates did not settle");
+    deferred += n;
+    if ((ls = pass(cur, n)) != LSYN_OK) return ls;
+    cur = 1 - cur;
     if ((e = take_snap()) != cudaSuccess) return c->cuda_fail(e, "snapshot");
     if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return c->cuda_fail(e, "resolve sync");
-    cur = 1 - cur;
+    if (std::min(c->h_snap[snap - 1].c.defer_n[cur], c->defer_cap) == 0 && (ls = close_holes()) != LSYN_OK) return ls;
   }
   const DevCounters& h = c->h_snap[snap - 1].c;
-  if (h.error) return c->fail(LSYN_E_STATE, "internal consistency check failed (code " + std::to_string(h.error) + ")");
-  uint32_t total = std::min(h.n_entries, c->max_entries);
-  if (h.holes_n) {
-    // Fill the id ranges warps reserved but left unused: move the entries
-    // above the level's dense end into them, so the level stays contiguous.
-    if (h.holes_n > c->hole_cap) return c->fail(LSYN_E_STATE, "hole log overflow");
-    std::vector<uint2> hr(h.holes_n);
-    e = cudaMemcpyAsync(hr.data(), c->holes, hr.size() * sizeof(uint2), cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    if (e != cudaSuccess) return c->cuda_fail(e, "hole log copy");
-    std::vector<uint2> mv;
-    const uint32_t dense_end = plan_hole_moves(hr.data(), unsigned(hr.size()), start, total, &mv);
-    if (mv.size() > c->move_cap) return c->fail(LSYN_E_STATE, "too many hole moves");
-    if (!mv.empty()) {
-      e = cudaMemcpyAsync(c->moves, mv.data(), mv.size() * sizeof(uint2), cudaMemcpyHostToDevice, c->stream);
-      if (e != cudaSuccess) return c->cuda_fail(e, "moves copy");
-      ev_begin();
-      e = c->word_bits == 32 ? Kernels<uint32_t>::fixup(cv, c->moves, unsigned(mv.size()), lc)
-                             : Kernels<uint64_t>::fixup(cv, c->moves, unsigned(mv.size()), lc);
-      ++launches;
-      if (e != cudaSuccess) return c->cuda_fail(e, "fixup kernel");
-      ev_end(3);
-    }
-    const unsigned de = dense_end;
-    e = cudaMemcpyAsync(&c->ctr->n_entries, &de, sizeof(unsigned), cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(&c->ctr->holes_n, 0, sizeof(unsigned), c->stream);
-    if (e == cudaSuccess && (e = take_snap()) == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    if (e != cudaSuccess) return c->cuda_fail(e, "fixup sync");
-    if (c->h_snap[snap - 1].c.error) return c->fail(LSYN_E_STATE, "hole fixup found an inconsistent slot");
-    total = dense_end;
+  if (h.error) {
+    static const char* const what[] = {"", "hash table probe overflow", "hole log overflow",
+                                       "hole fixup found an inconsistent slot", "inconsistent hole log"};
+    return c->fail(LSYN_E_STATE, std::string("internal consistency check failed: ") +
+                                     (h.error < 5 ? what[h.error] : "unknown code"));
   }
+  const uint32_t total = std::min(h.n_entries, c->max_entries);
   lsyn_status st = ctx_commit_level(c, k, c->h_snap[snap - 1].c, total, deferred, lp, out);
   if (st != LSYN_OK) return st;
   if (out) {

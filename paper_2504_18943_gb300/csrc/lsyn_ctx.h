@@ -128,6 +128,7 @@ struct lsyn_ctx {
   uint2* holes = nullptr;       // [hole_cap]
   unsigned hole_cap = 0;
   uint2* moves = nullptr;       // [move_cap]
+  unsigned* hole_bits = nullptr;  // [3 x hole_cap + 32] scratch of the device hole plan
   unsigned move_cap = 0;
   unsigned chunk = 1;
   char* fbuf = nullptr;

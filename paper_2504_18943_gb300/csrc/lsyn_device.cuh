@@ -1588,24 +1588,211 @@ static __global__ void k_batch_set_entries(const StepProblem* steps, const unsig
 // end into the holes below it (one warp per move): copy the CM row, its
 // provenance and slot index, and repoint the table slot to the new id.
 // ===========================================================================
-static __global__ void __launch_bounds__(256) k_fixup(CacheView cv, const uint2* moves, unsigned n) {
+static __global__ void __launch_bounds__(256) k_fixup(CacheView cv, const uint2* moves, unsigned n,
+                                                      const unsigned* n_dev) {
   const int lane = threadIdx.x & 31;
   const unsigned warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
+  if (n_dev) n = *n_dev;  // planned on the device (k_hole_plan)
   for (unsigned m = warp; m < n; m += nwarps) {
     const unsigned src = moves[m].x, dst = moves[m].y;
     const uint4* a = cv.arena + size_t(src) * cv.vecs;
     uint4* b = cv.arena + size_t(dst) * cv.vecs;
     for (unsigned v = lane; v < cv.vecs; v += 32) b[v] = a[v];
+    if (lane == 1) cv.prov[dst] = cv.prov[src];
+    if (lane == 2) cv.homes[dst] = cv.homes[src];
     if (lane == 0) {
-      cv.prov[dst] = cv.prov[src];
-      cv.homes[dst] = cv.homes[src];
       const unsigned sp = cv.slotpos[src];
       cv.slotpos[dst] = sp;
       const unsigned long long old = cv.table[sp];
       if (uint32_t(old) == src + 1u) cv.table[sp] = (old & 0xFFFFFFFF00000000ull) | (unsigned long long)(dst + 1u);
       else atomicExch(&cv.ctr->error, 3u);
     }
+  }
+}
+
+// Exclusive prefix sum over a block of exactly 1024 threads, one value per
+// thread; *total receives the block's sum (the same in every thread).
+__device__ __forceinline__ unsigned block_scan_1024(unsigned v, unsigned* total) {
+  __shared__ unsigned s_w[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_up_sync(kFull, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_w[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    unsigned t = s_w[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(kFull, t, o);
+      if (lane >= o) t += y;
+    }
+    s_w[lane] = t;
+  }
+  __syncthreads();
+  const unsigned before = w ? s_w[w - 1] : 0u;
+  *total = s_w[31];
+  __syncthreads();  // s_w is reused by the next call
+  return before + x - v;
+}
+
+// Hole plan of a level on the device, in two launches (no host round trip).
+// The hole log holds the id ranges [x, y) that warps reserved but left unused;
+// clipped to the level's range [start, total) they cover H ids, so the level's
+// dense end is total - H. The entries in [dense_end, total) (ids in no hole,
+// in id order) are the sources and the hole ids below dense_end (in log order)
+// the destinations of the moves, paired by rank: both lists have the same
+// length. Each logged range is at most 32 ids (a warp reserves at most 32 ids
+// at a time), so H <= 32 x hole_cap and the bitmap of [dense_end, total) fits
+// hole_cap words.
+//
+// Scratch layout (3 x hole_cap + 32 words): header [16] = {H, dense_end,
+// words, n}, bits [hole_cap] (holes in [dense_end, total)), word_pref
+// [hole_cap + 1] (live entries before each bitmap word), range_pref
+// [hole_cap + 1] (destinations before each logged range).
+struct HoleScratch {
+  unsigned* base;
+  unsigned cap;
+  __device__ unsigned* hdr() const { return base; }
+  __device__ unsigned* bits() const { return base + 16; }
+  __device__ unsigned* word_pref() const { return base + 16 + cap; }
+  __device__ unsigned* range_pref() const { return base + 16 + 2 * cap + 1; }
+};
+
+__device__ __forceinline__ unsigned hole_live_word(const unsigned* bits, unsigned w, unsigned words, unsigned H) {
+  unsigned m = ~__ldcg(bits + w);
+  if (w == words - 1u && (H & 31u)) m &= (1u << (H & 31u)) - 1u;
+  return m;
+}
+
+// Plan: one block of exactly 1024 threads. Sets ctr->moves_n (0 on an
+// inconsistent log, with ctr->error = 4), ctr->n_entries = dense_end and
+// ctr->holes_n = 0.
+static __global__ void __launch_bounds__(1024) k_hole_plan(DevCounters* ctr, const uint2* holes, unsigned hole_cap,
+                                                           unsigned start, unsigned max_entries, HoleScratch sc,
+                                                           unsigned move_cap) {
+  const unsigned t = threadIdx.x, T = blockDim.x;
+  const unsigned n = ctr->holes_n;
+  const unsigned total = min(ctr->n_entries, max_entries);
+  if (n > hole_cap || total < start) {  // an overflowed log (its warp set error 2) or no level range
+    if (t == 0) {
+      ctr->moves_n = 0;
+      atomicExch(&ctr->error, 4u);
+    }
+    return;
+  }
+  // 1. H and the dense end
+  unsigned h = 0;
+  for (unsigned i = t; i < n; i += T) {
+    const uint2 r = holes[i];
+    const unsigned lo = max(r.x, start), hi = min(r.y, total);
+    if (lo < hi) h += hi - lo;
+  }
+  unsigned H;
+  block_scan_1024(h, &H);
+  const unsigned words = (H + 31u) >> 5;
+  if (H > total - start || words > hole_cap) {
+    if (t == 0) {
+      ctr->moves_n = 0;
+      atomicExch(&ctr->error, 4u);
+    }
+    return;
+  }
+  const unsigned dense_end = total - H;
+  unsigned* bits = sc.bits();
+  for (unsigned w = t; w < words; w += T) bits[w] = 0u;
+  __syncthreads();
+  // 2. the holes at or above the dense end, as a bitmap of [dense_end, total)
+  for (unsigned i = t; i < n; i += T) {
+    const uint2 r = holes[i];
+    const unsigned lo = max(max(r.x, start), dense_end), hi = min(r.y, total);
+    for (unsigned id = lo; id < hi; ++id) atomicOr(&bits[(id - dense_end) >> 5], 1u << ((id - dense_end) & 31u));
+  }
+  __syncthreads();
+  // 3. live entries before each bitmap word (contiguous words per thread)
+  const unsigned per_w = (words + T - 1u) / T;
+  const unsigned w0 = min(t * per_w, words), w1 = min(w0 + per_w, words);
+  unsigned c = 0;
+  for (unsigned w = w0; w < w1; ++w) c += unsigned(__popc(hole_live_word(bits, w, words, H)));
+  unsigned n_src;
+  unsigned o = block_scan_1024(c, &n_src);
+  unsigned* wp = sc.word_pref();
+  for (unsigned w = w0; w < w1; ++w) {
+    wp[w] = o;
+    o += unsigned(__popc(hole_live_word(bits, w, words, H)));
+  }
+  // 4. destinations before each logged range (contiguous ranges per thread)
+  const unsigned per_r = (n + T - 1u) / T;
+  const unsigned r0 = min(t * per_r, n), r1 = min(r0 + per_r, n);
+  unsigned d = 0;
+  for (unsigned i = r0; i < r1; ++i) {
+    const uint2 r = holes[i];
+    const unsigned lo = max(r.x, start), hi = min(min(r.y, total), dense_end);
+    if (lo < hi) d += hi - lo;
+  }
+  unsigned n_dst;
+  unsigned od = block_scan_1024(d, &n_dst);
+  unsigned* rp = sc.range_pref();
+  for (unsigned i = r0; i < r1; ++i) {
+    rp[i] = od;
+    const uint2 r = holes[i];
+    const unsigned lo = max(r.x, start), hi = min(min(r.y, total), dense_end);
+    if (lo < hi) od += hi - lo;
+  }
+  if (t == 0) {
+    if (n_src != n_dst || n_src > move_cap) {
+      ctr->moves_n = 0;
+      atomicExch(&ctr->error, 4u);
+      return;
+    }
+    wp[words] = n_src;
+    rp[n] = n_dst;
+    unsigned* hd = sc.hdr();
+    hd[0] = H;
+    hd[1] = dense_end;
+    hd[2] = words;
+    hd[3] = n;
+    ctr->moves_n = n_src;
+    ctr->n_entries = dense_end;
+    ctr->holes_n = 0;
+  }
+}
+
+// Moves: thread per rank r < moves_n. The source is the r-th live entry of
+// [dense_end, total), the destination the r-th hole id below dense_end; both
+// are found by binary search over the plan's prefix arrays.
+static __global__ void __launch_bounds__(256) k_hole_moves(const DevCounters* ctr, const uint2* holes,
+                                                           unsigned start, HoleScratch sc, uint2* moves) {
+  const unsigned m = ctr->moves_n;
+  if (m == 0) return;
+  const unsigned* hd = sc.hdr();
+  const unsigned H = hd[0], dense_end = hd[1], words = hd[2], n = hd[3];
+  const unsigned* bits = sc.bits();
+  const unsigned* wp = sc.word_pref();
+  const unsigned* rp = sc.range_pref();
+  for (unsigned r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x) {
+    // last word w with wp[w] <= r (wp[0] = 0 <= r, wp[words] = m > r)
+    unsigned lo = 0, hi = words;
+    while (hi - lo > 1u) {
+      const unsigned mid = (lo + hi) >> 1;
+      if (__ldcg(wp + mid) <= r) lo = mid; else hi = mid;
+    }
+    unsigned live = hole_live_word(bits, lo, words, H);
+    for (unsigned k = r - __ldcg(wp + lo); k; --k) live &= live - 1u;
+    const unsigned src = dense_end + lo * 32u + unsigned(__ffs(live) - 1);
+    // last range i with rp[i] <= r (rp[0] = 0 <= r, rp[n] = m > r)
+    lo = 0;
+    hi = n;
+    while (hi - lo > 1u) {
+      const unsigned mid = (lo + hi) >> 1;
+      if (__ldcg(rp + mid) <= r) lo = mid; else hi = mid;
+    }
+    const unsigned dst = max(holes[lo].x, start) + (r - __ldcg(rp + lo));
+    moves[r] = make_uint2(src, dst);
   }
 }
 
@@ -1858,7 +2045,21 @@ template <typename W>
 cudaError_t Kernels<W>::fixup(const CacheView& cv, const uint2* moves, unsigned n, const LaunchCfg& lc) {
   if (n == 0) return cudaSuccess;
   const unsigned blocks = std::max(1u, std::min((n + 7u) / 8u, unsigned(lc.sms * 8)));
-  k_fixup<<<blocks, 256, 0, lc.stream>>>(cv, moves, n);
+  k_fixup<<<blocks, 256, 0, lc.stream>>>(cv, moves, n, nullptr);
+  return cudaGetLastError();
+}
+
+template <typename W>
+cudaError_t Kernels<W>::close_holes(const CacheView& cv, unsigned start, unsigned* bits, uint2* moves,
+                                    unsigned move_cap, const LaunchCfg& lc) {
+  const HoleScratch sc{bits, cv.hole_cap};
+  k_hole_plan<<<1, 1024, 0, lc.stream>>>(cv.ctr, cv.holes, cv.hole_cap, start, cv.max_entries, sc, move_cap);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_hole_moves<<<unsigned(lc.sms * 4), 256, 0, lc.stream>>>(cv.ctr, cv.holes, start, sc, moves);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // The move count is known on the device only: a full grid (warps past it exit at once).
+  k_fixup<<<unsigned(lc.sms * 8), 256, 0, lc.stream>>>(cv, moves, 0u, &cv.ctr->moves_n);
   return cudaGetLastError();
 }
 

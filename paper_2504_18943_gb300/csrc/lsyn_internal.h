@@ -52,6 +52,8 @@ struct DevCounters {
   unsigned long long built;      // candidates built in this level
   unsigned long long inserted;   // new entries written in this level
   unsigned long long work[8];    // tile counters of the persistent launches
+  unsigned int moves_n;          // hole moves planned on the device (k_hole_plan)
+  unsigned int pad1;
 };
 
 // Everything a kernel needs to probe, compare and insert (passed by value).
@@ -163,6 +165,11 @@ struct Kernels {
                             unsigned* error, const LaunchCfg& lc);
   // Move entries src -> dst (pairs), repointing their table slots.
   static cudaError_t fixup(const CacheView& cv, const uint2* moves, unsigned n, const LaunchCfg& lc);
+  // Plan the hole moves of the level starting at id `start` on the device
+  // (sets ctr->moves_n, ctr->n_entries = the dense end, ctr->holes_n = 0) and
+  // run them; no host round trip. `bits` is scratch of 3 x hole_cap + 32 words.
+  static cudaError_t close_holes(const CacheView& cv, unsigned start, unsigned* bits, uint2* moves, unsigned move_cap,
+                                 const LaunchCfg& lc);
   // Evaluate a postorder node list on every trace word of every plane:
   // scratch [n_nodes][planes][plane words]; a CM of planes x plane_vecs vectors.
   static cudaError_t eval(const uint4* atoms, const uint4* lenmask, unsigned plane_vecs, unsigned planes,
