@@ -67,8 +67,8 @@ Engine::~Engine() {
                   static_cast<void*>(h_fstatus_), static_cast<void*>(h_holes_)})
     if (p) cudaFreeHost(p);
   for (Lane& L : lanes_) {
-    for (void* p : {static_cast<void*>(L.snap), static_cast<void*>(L.h_holes), static_cast<void*>(L.h_val),
-                    static_cast<void*>(L.h_item), static_cast<void*>(L.h_text), static_cast<void*>(L.h_tst)})
+    for (void* p : {static_cast<void*>(L.snap), static_cast<void*>(L.h_val), static_cast<void*>(L.h_item),
+                    static_cast<void*>(L.h_text), static_cast<void*>(L.h_tst)})
       if (p) cudaFreeHost(p);
     if (L.ev) cudaEventDestroy(L.ev);
     if (L.stream) cudaStreamDestroy(L.stream);
@@ -139,10 +139,11 @@ lsyn_status Engine::init(const lsyn_config* cfg, const lsyn_batch_tuning* tune, 
   }
   for (Lane& L : lanes_) {
     L.d_moves = static_cast<uint2*>(mem_.get(sizeof(uint2) * size_t(move_cap_)));
+    L.d_bits = static_cast<unsigned*>(mem_.get(sizeof(unsigned) * (3 * size_t(hole_cap_) + 32)));
     L.d_item = static_cast<FormulaItem*>(mem_.get(sizeof(FormulaItem)));
     L.d_text = static_cast<char*>(mem_.get(kTextCap));
     L.d_tst = static_cast<int*>(mem_.get(sizeof(int)));
-    if (!L.d_moves || !L.d_item || !L.d_text || !L.d_tst || !pinned(&L.snap, 1) || !pinned(&L.h_holes, hole_cap_) ||
+    if (!L.d_moves || !L.d_bits || !L.d_item || !L.d_text || !L.d_tst || !pinned(&L.snap, 2) ||
         !pinned(&L.h_val, 1) || !pinned(&L.h_item, 1) || !pinned(&L.h_text, kTextCap) || !pinned(&L.h_tst, 1)) {
       err = "lane allocation failed";
       return LSYN_E_NOMEM;
@@ -1059,12 +1060,28 @@ lsyn_status Engine::lane_launch(Lane& L, Job* j, bool* progressed) {
     e = c->word_bits == 32 ? Kernels<uint32_t>::binary(cv, L.lp.plan, lc)
                            : Kernels<uint64_t>::binary(cv, L.lp.plan, lc);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(L.snap, c->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, L.stream);
+    e = cudaMemcpyAsync(&L.snap[0], c->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, L.stream);
+  // The first pass over the deferred candidates and the hole close are queued
+  // behind the level's kernels (both read their counts on the device).
+  if (e == cudaSuccess) e = cudaMemsetAsync(&c->ctr->defer_n[1], 0, sizeof(unsigned), L.stream);
+  if (e == cudaSuccess) {
+    CacheView rv = c->view(c->defer[1], &c->ctr->defer_n[1]);
+    rv.early_exit = 0;  // a deferred candidate must be settled even after a solution
+    e = c->word_bits == 32 ? Kernels<uint32_t>::desc_list(rv, c->defer[0], &c->ctr->defer_n[0], c->defer_cap, 0, lc)
+                           : Kernels<uint64_t>::desc_list(rv, c->defer[0], &c->ctr->defer_n[0], c->defer_cap, 0, lc);
+  }
+  if (e == cudaSuccess)
+    e = c->word_bits == 32 ? Kernels<uint32_t>::close_holes(cv, L.lp.start, L.d_bits, L.d_moves, move_cap_, lc)
+                           : Kernels<uint64_t>::close_holes(cv, L.lp.start, L.d_bits, L.d_moves, move_cap_, lc);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&L.snap[1], c->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, L.stream);
   if (e == cudaSuccess) e = cudaEventRecord(L.ev, L.stream);
   if (e != cudaSuccess) { err = std::string("large level: ") + cudaGetErrorString(e); return LSYN_E_CUDA; }
   L.j = j;
   L.k = k;
-  L.cur = 0;
+  L.cur = 1;
+  L.closed = true;
+  L.first = true;
   L.passes = 0;
   L.deferred = 0;
   L.total = 0;
@@ -1088,7 +1105,7 @@ lsyn_status Engine::lane_commit(Lane& L) {
   Job* j = L.j;
   lsyn_ctx* c = j->c;
   lsyn_level_stats st;
-  lsyn_status s = ctx_commit_level(c, L.k, *L.snap, L.total, L.deferred, L.lp, &st);
+  lsyn_status s = ctx_commit_level(c, L.k, L.snap[1], L.total, L.deferred, L.lp, &st);
   if (s != LSYN_OK) {
     lane_fail(L, s, c->err);
     return LSYN_OK;
@@ -1147,7 +1164,7 @@ lsyn_status Engine::lane_advance(Lane& L, bool* progressed) {
   Job* j = L.j;
   lsyn_ctx* c = j->c;
   const LaunchCfg lc{L.stream, sms_};
-  const DevCounters& h = *L.snap;
+  const DevCounters& h = L.snap[1];
   if (!L.ran) {
     L.ran = true;
     L.rec.run_ms = now_ms() - L.t_launched;
@@ -1156,6 +1173,15 @@ lsyn_status Engine::lane_advance(Lane& L, bool* progressed) {
   cudaError_t e = cudaSuccess;
   switch (L.stage) {
     case Lane::kRun: {
+      if (L.first) {  // the level's own deferred candidates were settled by the queued first pass
+        L.first = false;
+        const unsigned n0 = std::min(L.snap[0].defer_n[0], c->defer_cap);
+        if (n0) {
+          L.deferred += n0;
+          ++L.passes;
+          ++L.rec.passes;
+        }
+      }
       if (h.defer_overflow) { lane_fail(L, LSYN_E_STATE, "deferred list overflow"); return LSYN_OK; }
       if (h.error) { lane_fail(L, LSYN_E_STATE, "consistency check " + std::to_string(h.error) + " failed"); return LSYN_OK; }
       const unsigned nd = std::min(h.defer_n[L.cur], c->defer_cap);
@@ -1169,13 +1195,14 @@ lsyn_status Engine::lane_advance(Lane& L, bool* progressed) {
           e = c->word_bits == 32 ? Kernels<uint32_t>::desc_list(rv, c->defer[cur], &c->ctr->defer_n[cur], nd, 0, lc)
                                  : Kernels<uint64_t>::desc_list(rv, c->defer[cur], &c->ctr->defer_n[cur], nd, 0, lc);
         if (e == cudaSuccess)
-          e = cudaMemcpyAsync(L.snap, c->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, L.stream);
+          e = cudaMemcpyAsync(&L.snap[1], c->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, L.stream);
         if (e == cudaSuccess) e = cudaEventRecord(L.ev, L.stream);
         if (e != cudaSuccess) { err = std::string("deferred pass: ") + cudaGetErrorString(e); return LSYN_E_CUDA; }
         L.cur = 1 - cur;
         ++L.passes;
         ++L.rec.passes;
         L.deferred += nd;
+        L.closed = false;
         return LSYN_OK;
       }
       if (h.full && c->max_entries < j->cap_entries && (!h.solved || c->full_levels)) {
@@ -1185,43 +1212,20 @@ lsyn_status Engine::lane_advance(Lane& L, bool* progressed) {
         lane_done(L);
         return LSYN_OK;
       }
-      L.total = std::min(h.n_entries, c->max_entries);
-      if (h.holes_n) {
-        if (h.holes_n > hole_cap_) { lane_fail(L, LSYN_E_STATE, "hole log overflow"); return LSYN_OK; }
-        e = cudaMemcpyAsync(L.h_holes, c->holes, h.holes_n * sizeof(uint2), cudaMemcpyDeviceToHost, L.stream);
+      if (!L.closed) {  // close the holes the later passes left
+        const CacheView cv = c->view(c->defer[0], &c->ctr->defer_n[0]);
+        e = c->word_bits == 32 ? Kernels<uint32_t>::close_holes(cv, L.lp.start, L.d_bits, L.d_moves, move_cap_, lc)
+                               : Kernels<uint64_t>::close_holes(cv, L.lp.start, L.d_bits, L.d_moves, move_cap_, lc);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(&L.snap[1], c->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, L.stream);
         if (e == cudaSuccess) e = cudaEventRecord(L.ev, L.stream);
-        if (e != cudaSuccess) { err = std::string("hole log copy: ") + cudaGetErrorString(e); return LSYN_E_CUDA; }
-        L.stage = Lane::kHoles;
+        if (e != cudaSuccess) { err = std::string("hole fixup: ") + cudaGetErrorString(e); return LSYN_E_CUDA; }
+        L.closed = true;
         return LSYN_OK;
       }
+      L.total = std::min(h.n_entries, c->max_entries);
       return lane_commit(L);
     }
-    case Lane::kHoles: {
-      std::vector<uint2> mv;
-      const uint32_t dense = plan_hole_moves(L.h_holes, h.holes_n, L.lp.start, L.total, &mv);
-      if (mv.size() > move_cap_) { lane_fail(L, LSYN_E_STATE, "too many hole moves"); return LSYN_OK; }
-      const CacheView cv = c->view(c->defer[0], &c->ctr->defer_n[0]);
-      if (!mv.empty()) {
-        e = cudaMemcpyAsync(L.d_moves, mv.data(), mv.size() * sizeof(uint2), cudaMemcpyHostToDevice, L.stream);
-        if (e == cudaSuccess)
-          e = c->word_bits == 32 ? Kernels<uint32_t>::fixup(cv, L.d_moves, unsigned(mv.size()), lc)
-                                 : Kernels<uint64_t>::fixup(cv, L.d_moves, unsigned(mv.size()), lc);
-      }
-      *L.h_val = dense;
-      if (e == cudaSuccess)
-        e = cudaMemcpyAsync(&c->ctr->n_entries, L.h_val, sizeof(unsigned), cudaMemcpyHostToDevice, L.stream);
-      if (e == cudaSuccess) e = cudaMemsetAsync(&c->ctr->holes_n, 0, sizeof(unsigned), L.stream);
-      if (e == cudaSuccess)
-        e = cudaMemcpyAsync(L.snap, c->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, L.stream);
-      if (e == cudaSuccess) e = cudaEventRecord(L.ev, L.stream);
-      if (e != cudaSuccess) { err = std::string("hole fixup: ") + cudaGetErrorString(e); return LSYN_E_CUDA; }
-      L.total = dense;
-      L.stage = Lane::kFixed;
-      return LSYN_OK;
-    }
-    case Lane::kFixed:
-      if (h.error) { lane_fail(L, LSYN_E_STATE, "hole fixup found an inconsistent slot"); return LSYN_OK; }
-      return lane_commit(L);
     case Lane::kAnswer: {
       j->in_flight = false;
       if (*L.h_tst != 0) {

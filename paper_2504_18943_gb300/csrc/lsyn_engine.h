@@ -136,7 +136,7 @@ class Engine {
   };
   // A track of the large-level lane: one level of one job at a time.
   struct Lane {
-    enum Stage { kIdle, kRun, kHoles, kFixed, kAnswer };
+    enum Stage { kIdle, kRun, kAnswer };
     cudaStream_t stream = nullptr;
     cudaEvent_t ev = nullptr;
     Job* j = nullptr;
@@ -144,12 +144,13 @@ class Engine {
     int k = 0;
     LevelPlan lp;
     int cur = 0, passes = 0;
+    bool closed = false;           // the holes of every pass so far are closed
+    bool first = false;            // the first event of the level has not been handled
     unsigned long long deferred = 0;
     uint32_t total = 0;
-    DevCounters* snap = nullptr;   // pinned
-    uint2* h_holes = nullptr;      // pinned [hole_cap]
-    uint2* h_moves = nullptr;      // pinned [move_cap]
+    DevCounters* snap = nullptr;   // pinned [2]: after the level's kernels, latest
     uint2* d_moves = nullptr;      // device [move_cap]
+    unsigned* d_bits = nullptr;    // device [3 x hole_cap + 32]: hole plan scratch
     unsigned* h_val = nullptr;     // pinned scratch word
     FormulaItem* h_item = nullptr; // pinned, one item
     FormulaItem* d_item = nullptr;
