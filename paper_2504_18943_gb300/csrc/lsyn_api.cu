@@ -402,6 +402,7 @@ void lsyn::ctx_level_plan(lsyn_ctx* c, int k, LevelPlan* lp) {
   lp->u_first = c->level_start[k - 1];
   lp->u_count = lp->uops ? c->level_n[k - 1] : 0;
   lp->op_bytes_unary = double(lp->u_count) * M;
+  lp->cand_unary = double(lp->u_count) * double(__builtin_popcount(lp->uops));
   const uint32_t bops = ((m & LSYN_OP_AND) ? 1u : 0u) | ((m & LSYN_OP_OR) ? 2u : 0u) | ((m & LSYN_OP_U) ? 12u : 0u);
   if (!bops || k < 3) return;
   BinaryPlan& plan = lp->plan;
@@ -465,7 +466,9 @@ lsyn_status lsyn::ctx_commit_level(lsyn_ctx* c, int k, const DevCounters& h, uin
     out->deferred = int64_t(deferred);
     const double M = double(c->vecs) * 16.0;
     const double C = double(h.built), U = double(unique);
-    out->bytes_alg = lp.op_bytes_unary + lp.op_bytes_binary + C * 32.0 + (C - U) * M + U * (M + 16.0);
+    // a level that stopped at a solution read only part of its operands
+    const double done = planned > 0 ? std::min(1.0, C / double(planned)) : 1.0;
+    out->bytes_alg = (lp.op_bytes_unary + lp.op_bytes_binary) * done + C * 32.0 + (C - U) * M + U * (M + 16.0);
   }
   return LSYN_OK;
 }
@@ -807,15 +810,19 @@ lsyn_status lsyn_enumerate_level(lsyn_ctx* c, int32_t k, lsyn_level_stats* out) 
     // Per launch, from its exact built / inserted counters: operands, one table
     // sector per candidate, a compare read per duplicate, CM + provenance +
     // slot per insert.
-    auto launch_bytes = [&](int sn, double operands) {
+    // a launch that stopped at a solution read its operands only in part: in
+    // proportion to the candidates it built
+    auto launch_bytes = [&](int sn, double operands, double planned) {
       const DevCounters& b0 = c->h_snap[sn - 1].c;
       const DevCounters& b1 = c->h_snap[sn].c;
       const double Cl = double(b1.built - b0.built);
       const double Ul = double(b1.inserted - b0.inserted);
-      return operands + Cl * 32.0 + (Cl - Ul) * M + Ul * (M + 16.0);
+      const double done = planned > 0 ? std::min(1.0, Cl / planned) : 1.0;
+      return operands * done + Cl * 32.0 + (Cl - Ul) * M + Ul * (M + 16.0);
     };
-    if (binary_snap >= 0) out->bytes_binary = launch_bytes(binary_snap, lp.op_bytes_binary);
-    if (unary_snap >= 0) out->bytes_unary = launch_bytes(unary_snap, lp.op_bytes_unary);
+    const double planned = double(level_candidate_count(c, k) > 0 ? level_candidate_count(c, k) : 0);
+    if (binary_snap >= 0) out->bytes_binary = launch_bytes(binary_snap, lp.op_bytes_binary, planned - lp.cand_unary);
+    if (unary_snap >= 0) out->bytes_unary = launch_bytes(unary_snap, lp.op_bytes_unary, lp.cand_unary);
     if (c->timing) {
       for (int i = 0; i < evn; ++i) {
         float ms = 0;

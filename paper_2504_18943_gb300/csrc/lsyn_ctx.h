@@ -75,6 +75,7 @@ struct LevelPlan {
   uint32_t u_first = 0, u_count = 0;
   BinaryPlan plan;               // splits of the binary operators (plan.n_splits may be 0)
   double op_bytes_unary = 0, op_bytes_binary = 0;
+  double cand_unary = 0;         // candidates the unary launch builds when it runs to the end
 };
 
 // Language-cache sizing for a byte budget: the hash-table capacity (a power of

@@ -866,10 +866,16 @@ struct ListGen {
   __device__ uint64_t desc(int q) const { return d[q]; }
 };
 
+// Rows of level k-1 per warp batch of k_unary_c (4 operators each: 32
+// candidates, every lane probes): fewer warps fit than with 4-row batches
+// (the rows take shared memory), but each batch's round trips serve twice the
+// candidates, which measured faster.
+constexpr int kUnaryRowsC = 8;
+
 template <typename W>
-__global__ void __launch_bounds__(256, 4) k_unary_c(CacheView cv, uint32_t first, uint32_t count, uint32_t ops) {
+__global__ void __launch_bounds__(256, 3) k_unary_c(CacheView cv, uint32_t first, uint32_t count, uint32_t ops) {
   using P = PathC<W>;
-  constexpr int ROWS = 4;  // 16 candidates per batch
+  constexpr int ROWS = kUnaryRowsC;
   extern __shared__ uint4 smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   uint4* rows = smem + wib * (ROWS * 32 + P::kStage);
@@ -977,6 +983,65 @@ __global__ void __launch_bounds__(256, 4) k_binary_c(CacheView cv, BinaryPlan pl
       }
     }
     __syncthreads();
+  }
+  WarpDedup::flush(pend);
+  WarpDedup::retire(cv, idr);
+  if (lane == 0 && built) atomicAdd(&cv.ctr->built, built);
+}
+
+// Splits whose smaller level has fewer than kSmallSplitRows rows (the atoms
+// and the short first levels against a large level): a block tile of the small
+// level would give batches of fewer than 8 pairs. Here each warp stages 8 rows
+// of the larger level (`left`, in chunks of 8: lt_tiles chunks per split) in
+// shared memory and pairs them with every row of the smaller level (`right`,
+// read from L2), one full batch of 8 pairs x 4 operators per small row. The
+// candidate set is the split's; only the operand roles differ (and and or
+// commute, and both orders of U are built). Chunks are dealt to warps in
+// grid-stride order (every chunk is the same work); no block barrier.
+constexpr uint32_t kSmallSplitRows = 32;
+
+template <typename W>
+__global__ void __launch_bounds__(256, 3) k_binary_small_c(CacheView cv, BinaryPlan plan) {
+  using P = PathC<W>;
+  constexpr int ROWS = 8;
+  extern __shared__ uint4 smem[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  uint4* rows = smem + wib * (ROWS * 32 + P::kStage);
+  uint4* stage = rows + ROWS * 32;
+  typename P::Consts k;
+  P::load_consts(cv, k);
+  uint32_t en_ops = 0;
+#pragma unroll
+  for (int q = 0; q < 4 * ROWS; ++q) en_ops |= ((plan.ops >> (q & 3)) & 1u) << q;
+  BinaryGen<W> gen;
+  gen.a_rows = rows;
+  gen.steps = cv.steps;
+  gen.lane = lane;
+  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  unsigned long long built = 0;
+  typename P::Pending pend;
+  typename P::Ids idr;
+  for (unsigned long long c = warp; c < plan.total_tiles; c += nwarps) {
+    if (__any_sync(kFull, stop_requested(cv))) break;
+    int sp = 0;
+    while (sp + 1 < plan.n_splits && plan.s[sp + 1].tiles_begin <= c) ++sp;
+    const Split& S = plan.s[sp];
+    const uint32_t l0 = uint32_t(c - S.tiles_begin) * uint32_t(ROWS);
+    const uint32_t np = min(uint32_t(ROWS), S.left_n - l0);
+#pragma unroll
+    for (int p = 0; p < ROWS; ++p)
+      if (p < int(np)) rows[p * 32 + lane] = __ldg(row_ptr(cv, S.left_start + l0 + p) + lane);
+    __syncwarp();
+    gen.a0 = S.left_start + l0;
+    const uint32_t en = en_ops & (np >= 8u ? 0xFFFFFFFFu : ((1u << (4 * np)) - 1u));
+    for (uint32_t r = 0; r < S.right_n; ++r) {
+      gen.b_id = S.right_start + r;
+      gen.b = __ldg(row_ptr(cv, gen.b_id) + lane);
+      P::template batch<true>(cv, k, gen, int(4 * np), en, stage, pend, idr);
+      built += __popc(en);
+    }
+    __syncwarp();
   }
   WarpDedup::flush(pend);
   WarpDedup::retire(cv, idr);
@@ -1919,7 +1984,7 @@ struct LaunchA {
 
 template <typename W>
 struct LaunchC {
-  static constexpr size_t kUnarySmem = size_t(8) * (4 * 32 + PathC<W>::kStage) * sizeof(uint4);
+  static constexpr size_t kUnarySmem = size_t(8) * (kUnaryRowsC * 32 + PathC<W>::kStage) * sizeof(uint4);
   static constexpr size_t kDescSmem = size_t(8) * (PathC<W>::kStage + 16) * sizeof(uint4);
   static constexpr size_t kStageSmem = size_t(8) * PathC<W>::kStage * sizeof(uint4);
   static cudaError_t desc_list(const CacheView& cv, const unsigned long long* list, const unsigned int* list_n,
@@ -1930,20 +1995,61 @@ struct LaunchC {
     return cudaGetLastError();
   }
   static cudaError_t unary(const CacheView& cv, uint32_t first, uint32_t count, uint32_t ops, const LaunchCfg& lc) {
+    static bool once = (cudaFuncSetAttribute((const void*)k_unary_c<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             int(kUnarySmem)), true);
+    (void)once;
     static int occ = occupancy_blocks((const void*)k_unary_c<W>, 256, kUnarySmem);
-    const unsigned blocks = std::max(1u, std::min((count + 31u) / 32u, unsigned(lc.sms * occ)));
+    const unsigned blocks = std::max(1u, std::min((count + 63u) / 64u, unsigned(lc.sms * occ)));
     k_unary_c<W><<<blocks, 256, kUnarySmem, lc.stream>>>(cv, first, count, ops);
     return cudaGetLastError();
   }
   static cudaError_t binary(const CacheView& cv, const BinaryPlan& plan, const LaunchCfg& lc) {
     static bool once = (cudaFuncSetAttribute((const void*)k_binary_c<W>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024), true);
+    static bool once_s = (cudaFuncSetAttribute((const void*)k_binary_small_c<W>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, int(kUnarySmem)), true);
     (void)once;
-    const size_t smem = size_t(plan.tile) * 32 * sizeof(uint4) + kStageSmem;
-    const int occ = occupancy_blocks((const void*)k_binary_c<W>, 256, smem);
-    const unsigned long long blocks = std::max(1ull, std::min(plan.total_tiles, (unsigned long long)lc.sms * occ));
-    k_binary_c<W><<<unsigned(blocks), 256, smem, lc.stream>>>(cv, plan);
-    return cudaGetLastError();
+    (void)once_s;
+    // Splits with a small side go to k_binary_small_c (larger level as the
+    // per-warp staged operand, in chunks of 8 rows); the others keep the
+    // block tiles of k_binary_c. Both plans keep the splits' order.
+    BinaryPlan big = plan, small = plan;
+    big.n_splits = small.n_splits = 0;
+    big.total_tiles = small.total_tiles = 0;
+    for (int i = 0; i < plan.n_splits; ++i) {
+      Split sp = plan.s[i];
+      if (!sp.tri && sp.left_n < kSmallSplitRows) {
+        if (sp.right_n > sp.left_n) {
+          std::swap(sp.left_start, sp.right_start);
+          std::swap(sp.left_n, sp.right_n);
+        }
+        sp.lt_tiles = (sp.left_n + 7u) / 8u;
+        sp.rt_tiles = 1;
+        sp.tiles_begin = small.total_tiles;
+        small.total_tiles += sp.lt_tiles;
+        small.s[small.n_splits++] = sp;
+      } else {
+        sp.tiles_begin = big.total_tiles;
+        big.total_tiles += (unsigned long long)sp.lt_tiles * sp.rt_tiles;
+        big.s[big.n_splits++] = sp;
+      }
+    }
+    if (big.n_splits > 0) {
+      const size_t smem = size_t(big.tile) * 32 * sizeof(uint4) + kStageSmem;
+      const int occ = occupancy_blocks((const void*)k_binary_c<W>, 256, smem);
+      const unsigned long long blocks = std::max(1ull, std::min(big.total_tiles, (unsigned long long)lc.sms * occ));
+      k_binary_c<W><<<unsigned(blocks), 256, smem, lc.stream>>>(cv, big);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+    if (small.n_splits > 0) {
+      static int occ_s = occupancy_blocks((const void*)k_binary_small_c<W>, 256, kUnarySmem);
+      const unsigned long long blocks =
+          std::max(1ull, std::min((small.total_tiles + 7ull) / 8ull, (unsigned long long)lc.sms * occ_s));
+      k_binary_small_c<W><<<unsigned(blocks), 256, kUnarySmem, lc.stream>>>(cv, small);
+      return cudaGetLastError();
+    }
+    return cudaSuccess;
   }
 };
 
