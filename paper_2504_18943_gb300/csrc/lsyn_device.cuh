@@ -555,24 +555,60 @@ struct WarpDedup {
 
   // Ids this warp reserved from the shared counter and has not used yet:
   // [next, end). Reserving `chunk` ids per counter update keeps the counter
-  // off the critical path; what a warp leaves unused when it exits is logged
-  // as a hole and filled after the level (Kernels::fixup).
+  // cold; what a warp leaves unused when it exits is logged as a hole and
+  // filled after the level (Kernels::fixup). With full chunks (32 ids) the
+  // next chunk is reserved at the start of a batch whose inserts may need it
+  // (`pre`, in lane 0; `pre_ok` is warp-uniform): an atomic round trip is long
+  // under load, and this one then overlaps the batch's hashing and probing
+  // instead of delaying its inserts.
   struct Ids {
     unsigned next = 0, end = 0;
+    unsigned pre = 0;
+    bool pre_ok = false;
     unsigned long long inserted = 0;
   };
+
+  __device__ static void prefetch(const CacheView& cv, Ids& ids) {
+    if (!ids.pre_ok && ids.end - ids.next < 32u && cv.chunk >= 32u) {
+      if ((threadIdx.x & 31) == 0) ids.pre = atomicAdd(&cv.ctr->n_entries, cv.chunk);
+      ids.pre_ok = true;
+    }
+  }
+
+  // Ids for a batch's n_claim inserts when the current chunk holds `have`:
+  // the first fresh id (warp-uniform) once the chunk runs out; advances `ids`.
+  // Claim rank r takes ids.next + r while r < have, then fresh + (r - have).
+  __device__ static unsigned take(const Ids& ids, unsigned n_claim, unsigned have, unsigned base, bool use_pre) {
+    return n_claim > have ? __shfl_sync(kFull, use_pre ? ids.pre : base, 0) : 0u;
+  }
+  __device__ static void advance(const CacheView& cv, Ids& ids, unsigned n_claim, unsigned have, unsigned fresh,
+                                 bool use_pre) {
+    if (n_claim > have) {
+      ids.next = fresh + (n_claim - have);
+      ids.end = fresh + (use_pre ? cv.chunk : max(cv.chunk, n_claim - have));
+      if (use_pre) ids.pre_ok = false;
+    } else {
+      ids.next += n_claim;
+    }
+  }
+
+  __device__ static void log_hole(const CacheView& cv, unsigned lo, unsigned hi) {
+    if (lo < hi && lo < cv.max_entries) {
+      const unsigned h = atomicAdd(&cv.ctr->holes_n, 1u);
+      if (h < cv.hole_cap) cv.holes[h] = make_uint2(lo, min(hi, cv.max_entries));
+      else atomicExch(&cv.ctr->error, 2u);
+    }
+  }
 
   __device__ static void retire(const CacheView& cv, Ids& ids) {
     const int lane = threadIdx.x & 31;
     if (lane == 0) {
-      if (ids.next < ids.end && ids.next < cv.max_entries) {
-        const unsigned h = atomicAdd(&cv.ctr->holes_n, 1u);
-        if (h < cv.hole_cap) cv.holes[h] = make_uint2(ids.next, min(ids.end, cv.max_entries));
-        else atomicExch(&cv.ctr->error, 2u);
-      }
+      log_hole(cv, ids.next, ids.end);
+      if (ids.pre_ok) log_hole(cv, ids.pre, ids.pre + cv.chunk);
       if (ids.inserted) atomicAdd(&cv.ctr->inserted, ids.inserted);
     }
     ids.next = ids.end = 0;
+    ids.pre_ok = false;
     ids.inserted = 0;
   }
 
@@ -650,6 +686,7 @@ struct PathC {
   __device__ static void batch(const CacheView& cv, const Consts& k, const Gen& gen, int n, uint32_t en,
                                uint4* stage, Pending& pend, Ids& ids) {
     const int lane = threadIdx.x & 31;
+    WarpDedup::prefetch(cv, ids);
     uint32_t my_lo = 0, my_hi = 0, bad = 0;
     for (int q0 = 0; q0 < n; q0 += 4) {  // n is a multiple of 4: four operators per operand group
       uint4 c4[4];
@@ -753,12 +790,13 @@ struct PathC {
     const uint32_t claim = __ballot_sync(kFull, state == kClaimed);
     const unsigned n_claim = unsigned(__popc(claim));
     const unsigned have = ids.end - ids.next;  // warp-uniform
+    const bool use_pre = n_claim > have && ids.pre_ok;
     unsigned base = 0;
-    if (n_claim > have && lane == 0) base = atomicAdd(&cv.ctr->n_entries, max(cv.chunk, n_claim - have));
+    if (n_claim > have && !use_pre && lane == 0)
+      base = atomicAdd(&cv.ctr->n_entries, max(cv.chunk, n_claim - have));
     if (!kEarlyPublish) WarpDedup::flush(pend);  // overlaps the id reservation above
     if (claim) {
-      unsigned fresh = 0;
-      if (n_claim > have) fresh = __shfl_sync(kFull, base, 0);
+      const unsigned fresh = WarpDedup::take(ids, n_claim, have, base, use_pre);
       unsigned rank = 0;
       for (uint32_t m = claim; m; m &= m - 1u, ++rank) {
         const int q = __ffs(m) - 1;
@@ -767,12 +805,7 @@ struct PathC {
       }
       const unsigned my_rank = unsigned(__popc(claim & ((1u << lane) - 1u)));
       const unsigned my_id = my_rank < have ? ids.next + my_rank : fresh + (my_rank - have);
-      if (n_claim > have) {
-        ids.next = fresh + (n_claim - have);
-        ids.end = fresh + max(cv.chunk, n_claim - have);
-      } else {
-        ids.next += n_claim;
-      }
+      WarpDedup::advance(cv, ids, n_claim, have, fresh, use_pre);
       ids.inserted += __popc(__ballot_sync(kFull, state == kClaimed && my_id < cv.max_entries));
       if (state == kClaimed) {
         unsigned long long* slot = cv.table + pos;
@@ -1100,6 +1133,7 @@ struct PathD {
 
   template <bool kEarlyPublish, class Gen>
   __device__ static void batch(const CacheView& cv, const Gen& gen, int n, uint32_t en, Pending& pend, Ids& ids) {
+    WarpDedup::prefetch(cv, ids);
     const int lane = threadIdx.x & 31;
     const unsigned rv = cv.vecs >> 5;
     uint32_t my_lo = 0, my_hi = 0, bad = 0;
@@ -1183,12 +1217,13 @@ struct PathD {
     const uint32_t claim = __ballot_sync(kFull, state == kClaimed);
     const unsigned n_claim = unsigned(__popc(claim));
     const unsigned have = ids.end - ids.next;
+    const bool use_pre = n_claim > have && ids.pre_ok;
     unsigned base = 0;
-    if (n_claim > have && lane == 0) base = atomicAdd(&cv.ctr->n_entries, max(cv.chunk, n_claim - have));
+    if (n_claim > have && !use_pre && lane == 0)
+      base = atomicAdd(&cv.ctr->n_entries, max(cv.chunk, n_claim - have));
     if (!kEarlyPublish) WarpDedup::flush(pend);
     if (claim) {
-      unsigned fresh = 0;
-      if (n_claim > have) fresh = __shfl_sync(kFull, base, 0);
+      const unsigned fresh = WarpDedup::take(ids, n_claim, have, base, use_pre);
       unsigned rank = 0;
       for (uint32_t m = claim; m; m &= m - 1u, ++rank) {
         const int q = __ffs(m) - 1;
@@ -1200,12 +1235,7 @@ struct PathD {
       }
       const unsigned my_rank = unsigned(__popc(claim & ((1u << lane) - 1u)));
       const unsigned my_id = my_rank < have ? ids.next + my_rank : fresh + (my_rank - have);
-      if (n_claim > have) {
-        ids.next = fresh + (n_claim - have);
-        ids.end = fresh + max(cv.chunk, n_claim - have);
-      } else {
-        ids.next += n_claim;
-      }
+      WarpDedup::advance(cv, ids, n_claim, have, fresh, use_pre);
       ids.inserted += __popc(__ballot_sync(kFull, state == kClaimed && my_id < cv.max_entries));
       if (state == kClaimed) {
         unsigned long long* slot = cv.table + pos;
