@@ -428,7 +428,8 @@ void lsyn::ctx_level_plan(lsyn_ctx* c, int k, LevelPlan* lp) {
     sp.rt_tiles = (sp.right_n + plan.tile - 1) / plan.tile;
     sp.tiles_begin = tiles;
     sp.pairs_begin = pairs;
-    sp.pairs = (unsigned long long)sp.left_n * sp.right_n;
+    // a level with itself: the unordered pairs a < b (and, or and both orders of U)
+    sp.pairs = sp.tri ? (unsigned long long)sp.left_n * (sp.left_n - 1) / 2 : (unsigned long long)sp.left_n * sp.right_n;
     tiles += (unsigned long long)sp.lt_tiles * sp.rt_tiles;
     pairs += sp.pairs;
     lp->op_bytes_binary += double(sp.left_n + (sp.tri ? 0u : sp.right_n)) * M;

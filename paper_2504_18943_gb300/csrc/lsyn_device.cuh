@@ -338,6 +338,20 @@ __device__ __forceinline__ const uint4* row_ptr(const CacheView& cv, uint32_t id
   return cv.arena + size_t(id) * cv.vecs;
 }
 
+// Pair `local` of a split, as row offsets (left, right): row-major over
+// left x right, or, for a level paired with itself, the pairs a < b in order
+// of b (b = 1, 2, ...; a = 0 .. b-1), so that no pair index is wasted.
+__device__ __forceinline__ uint2 split_pair(const Split& S, unsigned long long local) {
+  if (!S.tri) {
+    const uint32_t ia = uint32_t(local / S.right_n);
+    return make_uint2(ia, uint32_t(local - (unsigned long long)ia * S.right_n));
+  }
+  unsigned long long b = (unsigned long long)((1.0 + sqrt(1.0 + 8.0 * double(local))) * 0.5);
+  while (b > 1 && b * (b - 1) / 2 > local) --b;
+  while ((b + 1) * b / 2 <= local) ++b;
+  return make_uint2(uint32_t(local - b * (b - 1) / 2), uint32_t(b));
+}
+
 // ===========================================================================
 // Path A: one thread holds a whole CM (V vectors, at most 128 bytes).
 // ===========================================================================
@@ -460,11 +474,8 @@ __global__ void __launch_bounds__(256) k_binary_a(CacheView cv, BinaryPlan plan)
     int sp = 0;
     while (sp + 1 < plan.n_splits && plan.s[sp + 1].pairs_begin <= p) ++sp;
     const Split& S = plan.s[sp];
-    const unsigned long long local = p - S.pairs_begin;
-    const uint32_t ia = uint32_t(local / S.right_n);
-    const uint32_t ib = uint32_t(local - (unsigned long long)ia * S.right_n);
-    if (S.tri && ia >= ib) continue;  // same level: unordered pairs a < b only
-    const uint32_t a_id = S.left_start + ia, b_id = S.right_start + ib;
+    const uint2 ab = split_pair(S, p - S.pairs_begin);
+    const uint32_t a_id = S.left_start + ab.x, b_id = S.right_start + ab.y;
     const bool full = ld_relaxed_u32(&cv.ctr->full) != 0u;
     uint4 a[V], b[V];
     P::load_row(row_ptr(cv, a_id), a);
@@ -1363,11 +1374,8 @@ __global__ void __launch_bounds__(256) k_binary_d(CacheView cv, BinaryPlan plan)
         int sp = 0;
         while (sp + 1 < plan.n_splits && plan.s[sp + 1].pairs_begin <= pidx) ++sp;
         const Split& S = plan.s[sp];
-        const unsigned long long local = pidx - S.pairs_begin;
-        const uint32_t ia = uint32_t(local / S.right_n);
-        const uint32_t ib = uint32_t(local - (unsigned long long)ia * S.right_n);
-        valid = !(S.tri && ia >= ib);
-        pr = make_uint2(S.left_start + ia, S.right_start + ib);
+        const uint2 ab = split_pair(S, pidx - S.pairs_begin);
+        pr = make_uint2(S.left_start + ab.x, S.right_start + ab.y);
       }
       s_pairs[wib][lane] = pr;
       ok = valid ? 1u : 0u;
@@ -1591,11 +1599,8 @@ __global__ void __launch_bounds__(256) k_batch_run(StepHeader* hdr, const StepPr
       bool valid = pidx < end;
       uint2 pr = make_uint2(0, 0);
       if (valid) {
-        const unsigned long long local = pidx - S.pairs_begin;
-        const uint32_t ia = uint32_t(local / S.right_n);
-        const uint32_t ib = uint32_t(local - (unsigned long long)ia * S.right_n);
-        valid = !(S.tri && ia >= ib);
-        pr = make_uint2(S.left_start + ia, S.right_start + ib);
+        const uint2 ab = split_pair(S, pidx - S.pairs_begin);
+        pr = make_uint2(S.left_start + ab.x, S.right_start + ab.y);
       }
       s_pairs[wib][lane] = pr;
       ok = valid ? 1u : 0u;

@@ -89,7 +89,7 @@ struct CacheView {
 struct Split {
   uint32_t left_start, left_n;   // rows of the smaller level (staged operand)
   uint32_t right_start, right_n; // rows of the other level (streamed operand)
-  uint32_t tri;                  // 1 when both sides are the same level: pairs a < b only
+  uint32_t tri;                  // 1 when both sides are the same level: pairs a < b only (pairs = n(n-1)/2)
   uint32_t lt_tiles, rt_tiles;   // tiles along each side
   uint32_t pad;
   unsigned long long tiles_begin;
