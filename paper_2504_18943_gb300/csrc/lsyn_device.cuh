@@ -579,6 +579,14 @@ struct WarpDedup {
     unsigned long long inserted = 0;
   };
 
+  // The arena-full flag, polled by every batch: once the arena is full each
+  // further claim leaves a tombstone in the table, so warps must stop
+  // claiming at once (a flag polled every few batches let the tombstones of
+  // a small table fill it). The flag has a cache line of its own.
+  __device__ static bool arena_full(const CacheView& cv) {
+    return __any_sync(kFull, (threadIdx.x & 31) == 0 && ld_relaxed_u32(&cv.ctr->full) != 0u);
+  }
+
   __device__ static void prefetch(const CacheView& cv, Ids& ids) {
     if (!ids.pre_ok && ids.end - ids.next < 32u && cv.chunk >= 32u) {
       if ((threadIdx.x & 31) == 0) ids.pre = atomicAdd(&cv.ctr->n_entries, cv.chunk);
@@ -724,7 +732,7 @@ struct PathC {
     // Once the arena is full this level can never be extended: only the spec
     // check (above) matters, so the rest of the batch skips the dedup instead
     // of filling the table with tombstones.
-    const bool full = __any_sync(kFull, lane == 0 && ld_relaxed_u32(&cv.ctr->full) != 0u);
+    const bool full = WarpDedup::arena_full(cv);
     int state = (mine && !full) ? WarpDedup::kProbing : WarpDedup::kDone;
     constexpr int kProbing = WarpDedup::kProbing, kDone = WarpDedup::kDone,
                   kClaimed = WarpDedup::kClaimed, kDeferred = WarpDedup::kDeferred;
@@ -1170,7 +1178,7 @@ struct PathD {
 
     constexpr int kProbing = WarpDedup::kProbing, kDone = WarpDedup::kDone,
                   kClaimed = WarpDedup::kClaimed, kDeferred = WarpDedup::kDeferred;
-    const bool full = __any_sync(kFull, lane == 0 && ld_relaxed_u32(&cv.ctr->full) != 0u);
+    const bool full = WarpDedup::arena_full(cv);
     int state = (mine && !full) ? kProbing : kDone;  // a full arena: spec check only
     const uint64_t h = h_fin(my_hi, my_lo);
     const unsigned long long tag = (h >> 32) << 32;
@@ -1537,7 +1545,7 @@ __global__ void __launch_bounds__(256) k_batch_run(StepHeader* hdr, const StepPr
     if (fresh && cv->vecs <= 8u) batch_a_load<W>(*cv, ca);
   };
   // 1. descriptors: atoms of problems at level 1, deferred re-examination
-  for (unsigned long long it = grab(&hdr->work[0]); it < hdr->total_d; it = grab(&hdr->work[0])) {
+  for (unsigned long long it = grab(&hdr->work[0].v); it < hdr->total_d; it = grab(&hdr->work[0].v)) {
     const int p = find_problem(steps, n, it, 0);
     enter(p);
     const StepProblem& sp = steps[p];
@@ -1560,7 +1568,7 @@ __global__ void __launch_bounds__(256) k_batch_run(StepHeader* hdr, const StepPr
     __syncwarp();
   }
   // 2. unary operators, 8 rows (32 candidates) per item
-  for (unsigned long long it = grab(&hdr->work[1]); it < hdr->total_u; it = grab(&hdr->work[1])) {
+  for (unsigned long long it = grab(&hdr->work[1].v); it < hdr->total_u; it = grab(&hdr->work[1].v)) {
     const int p = find_problem(steps, n, it, 1);
     enter(p);
     if (__any_sync(kFull, stop_requested(*cv))) continue;
@@ -1583,7 +1591,7 @@ __global__ void __launch_bounds__(256) k_batch_run(StepHeader* hdr, const StepPr
     bw.built += __popc(en);
   }
   // 3. binary operators, 8 pairs (32 candidates) per item
-  for (unsigned long long it = grab(&hdr->work[2]); it < hdr->total_b; it = grab(&hdr->work[2])) {
+  for (unsigned long long it = grab(&hdr->work[2].v); it < hdr->total_b; it = grab(&hdr->work[2].v)) {
     const int p = find_problem(steps, n, it, 2);
     enter(p);
     if (__any_sync(kFull, stop_requested(*cv))) continue;
@@ -1635,7 +1643,7 @@ __global__ void __launch_bounds__(256) k_batch_run(StepHeader* hdr, const StepPr
 // step's work counters.
 static __global__ void k_batch_begin(StepHeader* hdr, const StepProblem* steps, int n_max) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p == 0) hdr->work[0] = hdr->work[1] = hdr->work[2] = 0;
+  if (p == 0) hdr->work[0].v = hdr->work[1].v = hdr->work[2].v = 0;
   if (p >= n_max || p >= hdr->n) return;  // only the step's problems (slots past n are stale)
   DevCounters* c = steps[p].cv.ctr;
   c->full = 0;

@@ -37,24 +37,37 @@ constexpr uint32_t kSlotTomb = 0xFFFFFFFEu;     // claimed, but the arena was fu
 
 // Device-side counters of one context. The fields from `level_begin` on are
 // cleared at the start of every level.
-struct DevCounters {
+// Device counters of one language cache. Fields are grouped by how they are
+// used into 128-byte lines of their own: every warp bumps the id counter, polls
+// the flags and (rarely) appends to the deferred list, and operations on one
+// line are served one after another at one L2 slice, so a flag that shared the
+// counter's line waited behind its atomics.
+struct alignas(128) DevCounters {
+  // ---- the id counter (an atomic per warp chunk) ----
   unsigned int n_entries;        // arena fill (may exceed max_entries when full)
-  unsigned int pad0;
+  unsigned int pad0[31];
+  // ---- flags polled by every warp, written rarely ----
   unsigned long long sol;        // smallest descriptor of a separating candidate
-  // ---- per level ----
   unsigned int level_begin;      // marker (unused)
   unsigned int full;             // an insert found the arena full
   unsigned int solved;           // a separating candidate was found (early exit flag)
-  unsigned int error;            // probe ran over the whole table (cannot happen at load <= 0.9)
+  unsigned int error;            // internal consistency codes (probe overflow, hole log)
+  unsigned int pad1[26];
+  // ---- deferred lists and the hole log ----
   unsigned int defer_n[2];       // deferred-list fills (ping-pong)
   unsigned int defer_overflow;   // a deferred list overflowed: exactness lost
   unsigned int holes_n;          // id ranges reserved but left unused (hole log fill)
+  unsigned int pad2[28];
+  // ---- per-level totals (an atomic per warp at exit) and the hole plan ----
   unsigned long long built;      // candidates built in this level
   unsigned long long inserted;   // new entries written in this level
-  unsigned long long work[8];    // tile counters of the persistent launches
   unsigned int moves_n;          // hole moves planned on the device (k_hole_plan)
-  unsigned int pad1;
+  unsigned int pad3[27];
+  // ---- tile counters of the persistent launches ----
+  unsigned long long work[8];
+  unsigned int pad4[16];
 };
+static_assert(sizeof(DevCounters) == 640, "DevCounters: five 128-byte lines");
 
 // Everything a kernel needs to probe, compare and insert (passed by value).
 struct CacheView {
@@ -126,12 +139,18 @@ struct StepProblem {
 
 // Header of a batch step: item totals read by the persistent kernels, so one
 // captured graph serves every step.
-struct StepHeader {
+// The work-item counters (bumped by every warp) and the totals (read by every
+// warp) each have a 128-byte line of their own, as in DevCounters.
+struct alignas(128) StepHeader {
   unsigned long long total_u, total_b, total_d;
-  unsigned long long work[3];  // work-item counters of the three launches
   int n;                       // problems in this step
-  int pad[3];
+  int pad0[25];
+  struct alignas(128) Counter {
+    unsigned long long v;
+    unsigned long long pad[15];
+  } work[3];                   // work-item counters: descriptors, unary, binary
 };
+static_assert(sizeof(StepHeader) == 512, "StepHeader: four 128-byte lines");
 
 // Launch parameters chosen by the host.
 struct LaunchCfg {
