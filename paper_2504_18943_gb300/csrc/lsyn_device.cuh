@@ -1048,8 +1048,10 @@ __global__ void __launch_bounds__(256, 4) k_binary_c(CacheView cv, BinaryPlan pl
 // shared memory and pairs them with every row of the smaller level (`right`,
 // read from L2), one full batch of 8 pairs x 4 operators per small row. The
 // candidate set is the split's; only the operand roles differ (and and or
-// commute, and both orders of U are built). Chunks are dealt to warps in
-// grid-stride order (every chunk is the same work); no block barrier.
+// commute, and both orders of U are built). A work item is one chunk against
+// `group` rows of the small side (all of them unless the level is too small
+// to give every warp a few chunks: lt_tiles chunks x rt_tiles row groups);
+// items are dealt to warps in grid-stride order; no block barrier.
 constexpr uint32_t kSmallSplitRows = 32;
 
 template <typename W>
@@ -1079,7 +1081,11 @@ __global__ void __launch_bounds__(256, 3) k_binary_small_c(CacheView cv, BinaryP
     int sp = 0;
     while (sp + 1 < plan.n_splits && plan.s[sp + 1].tiles_begin <= c) ++sp;
     const Split& S = plan.s[sp];
-    const uint32_t l0 = uint32_t(c - S.tiles_begin) * uint32_t(ROWS);
+    const unsigned long long local = c - S.tiles_begin;
+    const uint32_t chunk = uint32_t(local / S.rt_tiles);
+    const uint32_t r0 = uint32_t(local - (unsigned long long)chunk * S.rt_tiles) * S.group;
+    const uint32_t r1 = min(r0 + S.group, S.right_n);
+    const uint32_t l0 = chunk * uint32_t(ROWS);
     const uint32_t np = min(uint32_t(ROWS), S.left_n - l0);
 #pragma unroll
     for (int p = 0; p < ROWS; ++p)
@@ -1087,7 +1093,7 @@ __global__ void __launch_bounds__(256, 3) k_binary_small_c(CacheView cv, BinaryP
     __syncwarp();
     gen.a0 = S.left_start + l0;
     const uint32_t en = en_ops & (np >= 8u ? 0xFFFFFFFFu : ((1u << (4 * np)) - 1u));
-    for (uint32_t r = 0; r < S.right_n; ++r) {
+    for (uint32_t r = r0; r < r1; ++r) {
       gen.b_id = S.right_start + r;
       gen.b = __ldg(row_ptr(cv, gen.b_id) + lane);
       P::template batch<true>(cv, k, gen, int(4 * np), en, stage, pend, idr);
@@ -2059,6 +2065,30 @@ struct LaunchC {
     BinaryPlan big = plan, small = plan;
     big.n_splits = small.n_splits = 0;
     big.total_tiles = small.total_tiles = 0;
+    static int occ_b = occupancy_blocks((const void*)k_binary_c<W>, 256, size_t(plan.tile) * 32 * sizeof(uint4) + kStageSmem);
+    static int occ_s = occupancy_blocks((const void*)k_binary_small_c<W>, 256, kUnarySmem);
+    unsigned long long chunks = 0;
+    for (int i = 0; i < plan.n_splits; ++i) {
+      const Split& sp = plan.s[i];
+      if (!sp.tri && sp.left_n < kSmallSplitRows) chunks += (std::max(sp.left_n, sp.right_n) + 7u) / 8u;
+    }
+    // a few work items per warp even at small levels: row groups of the small
+    // side when there are fewer chunks than that
+    const unsigned long long want_s = 4ull * lc.sms * occ_s * 8ull;
+    const unsigned long long per_chunk = chunks >= want_s || chunks == 0 ? 1ull : (want_s + chunks - 1) / chunks;
+    // block tiles of 32 rows, or 16 / 8 when 32 gives too few tiles to fill the GPU
+    auto tiles_of = [&](uint32_t t) {
+      unsigned long long n = 0;
+      for (int i = 0; i < plan.n_splits; ++i) {
+        const Split& sp = plan.s[i];
+        if (sp.tri || sp.left_n >= kSmallSplitRows)
+          n += (unsigned long long)((sp.left_n + t - 1) / t) * ((sp.right_n + t - 1) / t);
+      }
+      return n;
+    };
+    uint32_t tile = plan.tile;
+    while (tile > 8u && tiles_of(tile) < 2ull * lc.sms * occ_b) tile /= 2u;
+    big.tile = tile;
     for (int i = 0; i < plan.n_splits; ++i) {
       Split sp = plan.s[i];
       if (!sp.tri && sp.left_n < kSmallSplitRows) {
@@ -2067,11 +2097,14 @@ struct LaunchC {
           std::swap(sp.left_n, sp.right_n);
         }
         sp.lt_tiles = (sp.left_n + 7u) / 8u;
-        sp.rt_tiles = 1;
+        sp.group = std::max(1u, unsigned((sp.right_n + per_chunk - 1) / per_chunk));
+        sp.rt_tiles = (sp.right_n + sp.group - 1) / sp.group;
         sp.tiles_begin = small.total_tiles;
-        small.total_tiles += sp.lt_tiles;
+        small.total_tiles += (unsigned long long)sp.lt_tiles * sp.rt_tiles;
         small.s[small.n_splits++] = sp;
       } else {
+        sp.lt_tiles = (sp.left_n + tile - 1) / tile;
+        sp.rt_tiles = (sp.right_n + tile - 1) / tile;
         sp.tiles_begin = big.total_tiles;
         big.total_tiles += (unsigned long long)sp.lt_tiles * sp.rt_tiles;
         big.s[big.n_splits++] = sp;
@@ -2086,7 +2119,6 @@ struct LaunchC {
       if (e != cudaSuccess) return e;
     }
     if (small.n_splits > 0) {
-      static int occ_s = occupancy_blocks((const void*)k_binary_small_c<W>, 256, kUnarySmem);
       const unsigned long long blocks =
           std::max(1ull, std::min((small.total_tiles + 7ull) / 8ull, (unsigned long long)lc.sms * occ_s));
       k_binary_small_c<W><<<unsigned(blocks), 256, kUnarySmem, lc.stream>>>(cv, small);

@@ -103,8 +103,8 @@ struct Split {
   uint32_t left_start, left_n;   // rows of the smaller level (staged operand)
   uint32_t right_start, right_n; // rows of the other level (streamed operand)
   uint32_t tri;                  // 1 when both sides are the same level: pairs a < b only (pairs = n(n-1)/2)
-  uint32_t lt_tiles, rt_tiles;   // tiles along each side
-  uint32_t pad;
+  uint32_t lt_tiles, rt_tiles;   // tiles along each side (k_binary_small_c: chunks of 8 rows, row groups)
+  uint32_t group;                // k_binary_small_c: rows of the small side per work item
   unsigned long long tiles_begin;
   unsigned long long pairs_begin;
   unsigned long long pairs;
