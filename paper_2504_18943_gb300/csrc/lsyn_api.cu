@@ -390,6 +390,11 @@ void lsyn::ctx_level_plan(lsyn_ctx* c, int k, LevelPlan* lp) {
     const unsigned long long free_ids = c->max_entries > lp->start ? c->max_entries - lp->start : 0;
     const unsigned long long warps = (unsigned long long)c->sms * 24ull;
     c->chunk = unsigned(std::max(1ull, std::min(32ull, free_ids / (8ull * warps))));
+    // a small level: chunks no larger than its candidates spread over the
+    // warps, so that the ids warps leave unused (holes to close) stay few
+    const long long cand = level_candidate_count(c, k);
+    if (cand > 0)
+      c->chunk = unsigned(std::max(1ull, std::min<unsigned long long>(c->chunk, (unsigned long long)cand / (8ull * warps))));
   }
   const double M = double(c->vecs) * 16.0;
   if (k == 1) {

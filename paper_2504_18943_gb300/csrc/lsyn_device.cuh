@@ -1801,6 +1801,7 @@ static __global__ void __launch_bounds__(1024) k_hole_plan(DevCounters* ctr, con
   }
   // 1. H and the dense end
   unsigned h = 0;
+#pragma unroll 8
   for (unsigned i = t; i < n; i += T) {
     const uint2 r = holes[i];
     const unsigned lo = max(r.x, start), hi = min(r.y, total);
@@ -1821,6 +1822,7 @@ static __global__ void __launch_bounds__(1024) k_hole_plan(DevCounters* ctr, con
   for (unsigned w = t; w < words; w += T) bits[w] = 0u;
   __syncthreads();
   // 2. the holes at or above the dense end, as a bitmap of [dense_end, total)
+#pragma unroll 8
   for (unsigned i = t; i < n; i += T) {
     const uint2 r = holes[i];
     const unsigned lo = max(max(r.x, start), dense_end), hi = min(r.y, total);
@@ -1831,10 +1833,12 @@ static __global__ void __launch_bounds__(1024) k_hole_plan(DevCounters* ctr, con
   const unsigned per_w = (words + T - 1u) / T;
   const unsigned w0 = min(t * per_w, words), w1 = min(w0 + per_w, words);
   unsigned c = 0;
+#pragma unroll 8
   for (unsigned w = w0; w < w1; ++w) c += unsigned(__popc(hole_live_word(bits, w, words, H)));
   unsigned n_src;
   unsigned o = block_scan_1024(c, &n_src);
   unsigned* wp = sc.word_pref();
+#pragma unroll 8
   for (unsigned w = w0; w < w1; ++w) {
     wp[w] = o;
     o += unsigned(__popc(hole_live_word(bits, w, words, H)));
@@ -1843,6 +1847,7 @@ static __global__ void __launch_bounds__(1024) k_hole_plan(DevCounters* ctr, con
   const unsigned per_r = (n + T - 1u) / T;
   const unsigned r0 = min(t * per_r, n), r1 = min(r0 + per_r, n);
   unsigned d = 0;
+#pragma unroll 8
   for (unsigned i = r0; i < r1; ++i) {
     const uint2 r = holes[i];
     const unsigned lo = max(r.x, start), hi = min(min(r.y, total), dense_end);
@@ -1851,6 +1856,7 @@ static __global__ void __launch_bounds__(1024) k_hole_plan(DevCounters* ctr, con
   unsigned n_dst;
   unsigned od = block_scan_1024(d, &n_dst);
   unsigned* rp = sc.range_pref();
+#pragma unroll 8
   for (unsigned i = r0; i < r1; ++i) {
     rp[i] = od;
     const uint2 r = holes[i];
