@@ -96,6 +96,8 @@ class Engine {
   // when nothing else can move. *progressed says whether anything moved.
   lsyn_status pump(bool may_block, bool* progressed);
   bool busy() const { return !queue_.empty() || !active_.empty(); }
+  // A large level is on the GPU (its track waits for an event).
+  bool lanes_busy() const;
   // Jobs finished since the last call.
   std::vector<Job*> take_done();
   // Drop every job (queued, active or resident) and free their slots.
@@ -238,7 +240,6 @@ class Engine {
   lsyn_status launch_plain(int word_bits, int n, int sms);
   lsyn_status answer(const std::vector<Job*>& solved);
   // large-level lane
-  bool lanes_busy() const;
   lsyn_status lane_advance(Lane& L, bool* progressed);
   lsyn_status lane_launch(Lane& L, Job* j, bool* progressed);
   lsyn_status lane_commit(Lane& L);

@@ -109,9 +109,18 @@ void lsyn_server::loop() {
       return;
     }
     if (!done.empty()) cv_done.notify_all();
-    // Only a large level is in flight: look again shortly, or at once if a
-    // submission arrives (it may join the batch steps meanwhile).
-    if (!moved && done.empty()) cv_work.wait_for(lk, std::chrono::microseconds(100), [&] { return stop || !inbox.empty(); });
+    // Nothing moved. While a large level is on the GPU, poll it closely (a
+    // timed wait sleeps for its duration plus the timer slack, and a heavy
+    // problem passes here once per level); otherwise wait for a submission
+    // or look again shortly.
+    if (!moved && done.empty()) {
+      if (eng.lanes_busy()) {
+        lk.unlock();
+        std::this_thread::yield();
+      } else {
+        cv_work.wait_for(lk, std::chrono::microseconds(100), [&] { return stop || !inbox.empty(); });
+      }
+    }
   }
 }
 
