@@ -520,7 +520,9 @@ def _kernel_sha() -> str:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 30 solves for the mid workload, about half a second on the GPU, "
+                         "so that the clock sampler sees it; 3 for the reference arm and the batched workload)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lsyn", choices=["lsyn", "reference"])
     ap.add_argument("--seed", type=int, default=2)
@@ -534,6 +536,8 @@ def main():
     ap.add_argument("--rates", default="50,200,1000", help="served: arrival rates (problems/s)")
     ap.add_argument("--duration", type=float, default=60.0, help="served: seconds of arrivals per rate")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 30 if (args.impl == "lsyn" and args.workload == "mid") else 3
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":
