@@ -164,7 +164,7 @@ def run_reference(args):
             "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
                              "sample": f"levels 1..{args.ref_levels} of the mid-scale problem per step"},
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line))
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -317,7 +317,7 @@ def run_lsyn(args):
             "clocks": clocks.summary(),
             "levels": per_level,
         }
-        print(json.dumps(line))
+        print(json.dumps(line), flush=True)
     L.lsyn_destroy(ctx)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -438,7 +438,7 @@ def run_batched(args):
                     "h2d_bytes_per_step": sum(q.h2d_bytes for q in packed), "d2h_bytes_per_step": BATCH_N * 4096},
             "gpu_launches": None, "clocks": clocks.summary(),
         }
-        print(json.dumps(line))
+        print(json.dumps(line), flush=True)
     return 0
 
 
@@ -504,7 +504,7 @@ def run_served(args):
                     "h2d_bytes_per_step": None, "d2h_bytes_per_step": None},
             "gpu_launches": None,
         }
-        print(json.dumps(line))
+        print(json.dumps(line), flush=True)
     return 0
 
 

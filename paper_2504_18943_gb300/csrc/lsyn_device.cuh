@@ -1042,8 +1042,10 @@ __global__ void __launch_bounds__(256, 4) k_binary_c(CacheView cv, BinaryPlan pl
 }
 
 // Splits whose smaller level has fewer than kSmallSplitRows rows (the atoms
-// and the short first levels against a large level): a block tile of the small
-// level would give batches of fewer than 8 pairs. Here each warp stages 8 rows
+// against a large level): a block tile of the small level would give batches
+// of fewer than 8 pairs. (Up to 16 rows measured the same as 8; at 32 and
+// above the block tiles of k_binary_c were faster, the row reuse of a shared
+// tile outweighing partly filled batches.) Here each warp stages 8 rows
 // of the larger level (`left`, in chunks of 8: lt_tiles chunks per split) in
 // shared memory and pairs them with every row of the smaller level (`right`,
 // read from L2), one full batch of 8 pairs x 4 operators per small row. The
@@ -1052,7 +1054,7 @@ __global__ void __launch_bounds__(256, 4) k_binary_c(CacheView cv, BinaryPlan pl
 // `group` rows of the small side (all of them unless the level is too small
 // to give every warp a few chunks: lt_tiles chunks x rt_tiles row groups);
 // items are dealt to warps in grid-stride order; no block barrier.
-constexpr uint32_t kSmallSplitRows = 32;
+constexpr uint32_t kSmallSplitRows = 16;
 
 template <typename W>
 __global__ void __launch_bounds__(256, 3) k_binary_small_c(CacheView cv, BinaryPlan plan) {

@@ -340,16 +340,36 @@ def lsyn_version() -> str:
     return _lib.lsyn_version().decode()
 
 
+# Configurations whose allocation callbacks a live handle (context, batch or
+# server) may still call, by handle value. The library keeps the function
+# pointers of a config's alloc / free callbacks and calls free when the handle
+# is destroyed, so the Python callback objects must outlive that call even
+# when the caller passed a temporary config.
+_live_configs: dict = {}
+
+
+def _hold(handle: ctypes.c_void_p, config) -> None:
+    if config is not None and handle.value:
+        _live_configs[handle.value] = config
+
+
+def _let_go(handle) -> None:
+    value = handle.value if isinstance(handle, ctypes.c_void_p) else handle
+    _live_configs.pop(value, None)
+
+
 def lsyn_create(problem: PackedProblem, config: Optional[lsyn_config] = None) -> ctypes.c_void_p:
     ctx = ctypes.c_void_p()
     st = _lib.lsyn_create(ctypes.byref(problem.struct), ctypes.byref(config) if config is not None else None,
                           ctypes.byref(ctx))
     _check(st, None)
+    _hold(ctx, config)
     return ctx
 
 
 def lsyn_destroy(ctx) -> None:
     _lib.lsyn_destroy(ctx)
+    _let_go(ctx)  # after the library's last call into the config's free callback
 
 
 def lsyn_last_error(ctx=None) -> str:
@@ -515,6 +535,7 @@ def lsyn_batch_create(problems: Sequence[PackedProblem], config: Optional[lsyn_c
                                 ctypes.byref(tuning) if tuning is not None else None, ctypes.byref(b))
     if st != LSYN_OK:
         raise LsynError(st, _batch_err(None))
+    _hold(b, config)
     return b
 
 
@@ -549,6 +570,7 @@ def lsyn_batch_problem(batch, i: int) -> ctypes.c_void_p:
 
 def lsyn_batch_destroy(batch) -> None:
     _lib.lsyn_batch_destroy(batch)
+    _let_go(batch)
 
 
 def _trace(fn, handle, cap: int = 4096) -> list:
@@ -654,6 +676,7 @@ def lsyn_server_create(config: Optional[lsyn_config] = None,
                                  ctypes.byref(tuning) if tuning is not None else None, ctypes.byref(sv))
     if st != LSYN_OK:
         raise LsynError(st, _server_err(None))
+    _hold(sv, config)
     return sv
 
 
@@ -694,6 +717,7 @@ def lsyn_server_stats(server) -> dict:
 
 def lsyn_server_destroy(server) -> None:
     _lib.lsyn_server_destroy(server)
+    _let_go(server)
 
 
 class Server:
