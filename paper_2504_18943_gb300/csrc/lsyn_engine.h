@@ -10,7 +10,8 @@
 //  * a level with more candidates than the solo threshold runs in the
 //    large-level lane: the one-problem kernels on a stream of their own, one
 //    job's level after another in admission order, driven by a non-blocking
-//    state machine (launch, deferred passes, hole fixup, commit, answer) that
+//    state machine (launch with the first deferred pass and the level's hole
+//    close queued behind it; further deferred passes; commit; answer) that
 //    the host advances between batch steps. While small levels are in the
 //    system the large-level launches leave `light_sms` SMs to them.
 //
