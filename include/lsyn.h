@@ -118,6 +118,30 @@ typedef void (*lsyn_free_fn)(void* ptr, void* user);
  *                allocator); NULL = cudaMalloc / cudaFree.
  *   stream       cudaStream_t for all device work; NULL = the legacy default stream.
  *   device       CUDA device ordinal; -1 or 0..n-1 (the current device if -1).
+ *   tile_rows    0: automatic; 8, 16 or 32: rows of each side of the block
+ *                tiles of the binary launch for 512-byte CMs (k_binary_c),
+ *                kept at every level. By default a tile starts at 32 rows and
+ *                is halved (to 16, then 8) while the level gives fewer than
+ *                two tiles per resident block. The tile changes only the order
+ *                in which pairs are visited, never a level's set of CMs; the
+ *                field exists so that each tile size can be checked at any
+ *                level. Other values: LSYN_E_INVAL.
+ *   defer_cap    entries of each of the two deferred-candidate lists; 0 =
+ *                automatic (cache entries / 16, within 2^16..2^23). A level
+ *                that defers more candidates than this fails with
+ *                LSYN_E_STATE ("deferred list overflow").
+ *   hole_cap     entries of the hole log (id ranges warps reserved and left
+ *                unused, closed after each level); 0 = 2^16. A level that
+ *                logs more fails with LSYN_E_STATE. After either failure the
+ *                context must be reset (lsyn_reset) before it is used again.
+ *   time_limit_ms  0: none. Otherwise lsyn_solve checks, before building each
+ *                level after the first one it builds, whether this much time
+ *                has passed since it was called, and if so stops with
+ *                LSYN_E_TIMEOUT; the levels built so far stay complete and a
+ *                later lsyn_solve continues from them. A level that has
+ *                started is not interrupted.
+ * The fields after `device` were added later; a zero-filled struct keeps every
+ * default.
  */
 typedef struct {
   uint32_t op_mask;
@@ -130,6 +154,10 @@ typedef struct {
   void* alloc_user;
   void* stream;
   int32_t device;
+  int32_t tile_rows;
+  uint32_t defer_cap;
+  uint32_t hole_cap;
+  double time_limit_ms;
 } lsyn_config;
 
 /* Per-level statistics (filled by lsyn_enumerate_level). */
@@ -212,7 +240,9 @@ lsyn_status lsyn_enumerate_level(lsyn_ctx* ctx, int32_t k, lsyn_level_stats* out
  * passed. On LSYN_OK out->formula holds a separating formula of minimal size
  * out->size (minimal when out->exact is 1). Returns LSYN_NOT_FOUND when no
  * formula up to max_size separates, LSYN_E_CACHE_FULL when the cache filled up
- * before a solution was found (levels up to out->levels_done are exact).
+ * before a solution was found (levels up to out->levels_done are exact), and
+ * LSYN_E_TIMEOUT when config->time_limit_ms passed before a level could start
+ * (out->levels_done complete levels are kept; calling again continues).
  */
 lsyn_status lsyn_solve(lsyn_ctx* ctx, int32_t max_size, lsyn_result* out);
 
@@ -474,12 +504,16 @@ void lsyn_server_destroy(lsyn_server* server);
  * Per-node scratch lives in a fixed 8 MiB device array inside the library,
  * one per GPU, held until the process exits: (nodes x n_traces x word_bits/8)
  * must not exceed 8 MiB and a formula may have at most 960 nodes, otherwise
- * LSYN_E_INVAL with a message in lsyn_last_error(NULL). The first call on a
- * device looks the array's device address up once (cudaGetSymbolAddress);
- * make that first call before capturing the stream into a graph. Every call
- * shares the array and it keeps the last call's contents (nothing in it needs
- * clearing); calls that overlap on the GPU race on it. No cudaMalloc, cudaFree
- * or other allocating routine is called.
+ * LSYN_E_INVAL with a message in lsyn_last_error(NULL). The CUDA runtime loads
+ * the library's device code lazily, so the array is reserved on a device when
+ * the first call there loads this entry point's code (that first call also
+ * looks the array's device address up, with cudaGetSymbolAddress): it may
+ * allocate and synchronise inside the driver. Make that first call on each
+ * device as a warm-up (a one-node formula will do) before a memory manager
+ * claims the GPU's memory, and before capturing the stream into a graph.
+ * Every call shares the array and it keeps the last call's contents (nothing
+ * in it needs clearing); calls that overlap on the GPU race on it. The call
+ * itself invokes no cudaMalloc, cudaFree or other allocating routine.
  */
 lsyn_status lsyn_eval_noalloc(int32_t n_props, int32_t n_traces, int32_t word_bits, const void* atom_words,
                               const int32_t* lengths, const char* formula, void* dst, void* stream);

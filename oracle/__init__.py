@@ -81,6 +81,8 @@ def _configure(lib) -> None:
     for name in ("oracle_level_cm", "oracle_level_formula"):
         getattr(lib, name).restype = i32
         getattr(lib, name).argtypes = [vp, i32, i64, ctypes.c_char_p, sz]
+    lib.oracle_level_cm_rows.restype = i64
+    lib.oracle_level_cm_rows.argtypes = [vp, i32, i64, i64, ctypes.c_char_p, sz]
     lib.oracle_solve.restype = i32
     lib.oracle_solve.argtypes = [vp, i32, ctypes.c_uint, ctypes.c_char_p, sz, ctypes.POINTER(i64)]
 
@@ -190,6 +192,17 @@ class Run:
                 raise RuntimeError("cm export failed")
             out.append(buf.value.decode())
         return out
+
+    def cm_rows(self, k: int, first: int = 0, count: Optional[int] = None) -> np.ndarray:
+        """Characteristic matrices of entries [first, first + count) of level k
+        as a uint8 array [count, stride]: each row is one matrix's '0'/'1'
+        text (traces joined by ','), padded with zero bytes."""
+        n = self.size(k) - first if count is None else count
+        stride = int(self.spec.lengths.sum()) + self.spec.n_traces
+        buf = ctypes.create_string_buffer(max(1, n * stride))
+        if self._lib.oracle_level_cm_rows(self._h, k, first, n, buf, stride) != n:
+            raise RuntimeError("cm export failed")
+        return np.frombuffer(buf, dtype=np.uint8, count=n * stride).reshape(n, stride)
 
     def formulas(self, k: int) -> List[str]:
         buf = ctypes.create_string_buffer(1 << 16)

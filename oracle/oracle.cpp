@@ -536,6 +536,20 @@ int oracle_level_cm(const void* run, int k, int64_t idx, char* buf, size_t cap) 
   return copy_out(join(r.levels[k][idx].cm), buf, cap);
 }
 
+// Entries [first, first + count) of level k, each characteristic matrix (as
+// oracle_level_cm gives it) in a row of its own of `stride` bytes, padded
+// with zero bytes. Returns the rows written, -1 on a bad range, -2 if a
+// matrix does not fit a row. A plain copy, for exporting large levels.
+int64_t oracle_level_cm_rows(const void* run, int k, int64_t first, int64_t count, char* buf, size_t stride) {
+  if (first < 0 || count < 0 || first + count > oracle_level_size(run, k)) return -1;
+  for (int64_t r = 0; r < count; ++r) {
+    char* row = buf + (size_t)r * stride;
+    std::memset(row, 0, stride);
+    if (oracle_level_cm(run, k, first + r, row, stride) < 0) return -2;
+  }
+  return count;
+}
+
 // One formula with that characteristic matrix.
 int oracle_level_formula(const void* run, int k, int64_t idx, char* buf, size_t cap) {
   const Run& r = *static_cast<const Run*>(run);

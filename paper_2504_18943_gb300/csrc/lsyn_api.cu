@@ -414,6 +414,10 @@ void lsyn::ctx_level_plan(lsyn_ctx* c, int k, LevelPlan* lp) {
   plan.ops = bops;
   plan.work_slot = 0;
   plan.tile = c->path == 2 ? std::max(1u, std::min(32u, unsigned((48 * 1024) / (c->vecs * 16)))) : 1u;
+  if (c->path == 2 && c->tile_rows) {
+    plan.tile = c->tile_rows;
+    plan.tile_fixed = 1;
+  }
   unsigned long long tiles = 0, pairs = 0;
   for (int i = 1; 2 * i <= k - 1; ++i) {
     const int j = k - 1 - i;
@@ -541,6 +545,11 @@ lsyn_status lsyn::ctx_shell(const lsyn_problem* problem, const lsyn_config* conf
   const double load = cfg.table_load > 0 ? cfg.table_load : 0.5;
   if (!(load > 0 && load <= 0.9)) { g_create_error = "table_load must be in (0, 0.9]"; return LSYN_E_INVAL; }
   const unsigned long long cache_bytes = cfg.cache_bytes ? cfg.cache_bytes : (1ull << 30);
+  if (cfg.tile_rows != 0 && cfg.tile_rows != 8 && cfg.tile_rows != 16 && cfg.tile_rows != 32) {
+    g_create_error = "tile_rows must be 0, 8, 16 or 32";
+    return LSYN_E_INVAL;
+  }
+  if (!(cfg.time_limit_ms >= 0)) { g_create_error = "time_limit_ms must be >= 0"; return LSYN_E_INVAL; }
 
   // Paths: A (thread per candidate) up to 128 bytes, padded to a power of two
   // of 16-byte vectors; C (one vector per lane) up to 512 bytes; D (whole
@@ -594,8 +603,10 @@ lsyn_status lsyn::ctx_shell(const lsyn_problem* problem, const lsyn_config* conf
   c->path = vecs <= 8 ? 1 : vecs == 32 ? 2 : 3;
   c->table_cap = best_cap;
   c->max_entries = unsigned(best_e);
-  c->defer_cap = unsigned(std::max(1ull << 16, std::min(1ull << 23, best_e / 16)));
-  c->hole_cap = 1u << 16;
+  c->defer_cap = cfg.defer_cap ? cfg.defer_cap : unsigned(std::max(1ull << 16, std::min(1ull << 23, best_e / 16)));
+  c->hole_cap = cfg.hole_cap ? std::min(cfg.hole_cap, 1u << 24) : 1u << 16;
+  c->tile_rows = unsigned(cfg.tile_rows);
+  c->time_limit_ms = cfg.time_limit_ms;
   c->move_cap = c->hole_cap * 32u;
   cudaError_t e;
   if (cfg.device >= 0 && (e = cudaSetDevice(cfg.device)) != cudaSuccess) {
@@ -850,7 +861,14 @@ lsyn_status lsyn_solve(lsyn_ctx* c, int32_t max_size, lsyn_result* out) {
   out->exact = 0;
   out->launches = 0;
   lsyn_status result = LSYN_NOT_FOUND;
-  for (int k = c->levels_done + 1; k <= max_size; ++k) {
+  const int first_k = c->levels_done + 1;
+  for (int k = first_k; k <= max_size; ++k) {
+    // the deadline is checked between levels: the first level of the call always runs
+    if (c->time_limit_ms > 0 && k > first_k && now_ms() - t0 >= c->time_limit_ms) {
+      c->err = "time limit of " + std::to_string(c->time_limit_ms) + " ms passed before level " + std::to_string(k);
+      result = LSYN_E_TIMEOUT;
+      break;
+    }
     lsyn_level_stats st;
     lsyn_status s = lsyn_enumerate_level(c, k, &st);
     if (s != LSYN_OK) { result = s; break; }

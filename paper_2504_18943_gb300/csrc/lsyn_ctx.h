@@ -107,6 +107,8 @@ struct lsyn_ctx {
   bool borrowed = false;   // owned by a batch or server: not driven or destroyed through the handle
   bool owns_host = false;  // h_snap / h_fbuf / h_fstatus are this context's pinned buffers
   double table_load = 0.5;
+  unsigned tile_rows = 0;      // forced block-tile rows of the 512-byte binary launch (0: automatic)
+  double time_limit_ms = 0;    // lsyn_solve's deadline between levels (0: none)
   // problem
   int n_props = 0, n_pos = 0, n_neg = 0, T = 0, word_bits = 32, max_len = 1, steps = 0;
   unsigned vecs = 0;

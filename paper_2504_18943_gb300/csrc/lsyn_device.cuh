@@ -311,6 +311,18 @@ __device__ __forceinline__ void st_release(unsigned long long* p, unsigned long 
   asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
+// One probe of a table slot: claims it if empty (0), else returns what is
+// there. Acquire semantics: when the value is a published id, the writer's
+// release (fence.acq_rel.gpu, then a relaxed store of the slot) synchronises
+// with this read, so the entry's CM row, stored before the release, is visible
+// to this thread's later reads, and, after a warp barrier, to its warp's.
+__device__ __forceinline__ unsigned long long cas_acquire(unsigned long long* p, unsigned long long cmp,
+                                                          unsigned long long val) {
+  unsigned long long old;
+  asm volatile("atom.acquire.gpu.global.cas.b64 %0, [%1], %2, %3;" : "=l"(old) : "l"(p), "l"(cmp), "l"(val) : "memory");
+  return old;
+}
+
 __device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
   unsigned v;
   asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -394,7 +406,7 @@ struct PathA {
     for (unsigned long long it = 0; it <= cv.table_mask; ++it, pos = (pos + 1) & cv.table_mask) {
       unsigned long long* slot = cv.table + pos;
       // One atomic per probe: claims an empty slot, or returns what is there.
-      const unsigned long long sv = atomicCAS(slot, 0ull, tag | kSlotPending);
+      const unsigned long long sv = cas_acquire(slot, 0ull, tag | kSlotPending);
       if (sv == 0ull) {
         const unsigned id = atomicAdd(&cv.ctr->n_entries, 1u);
         if (id >= cv.max_entries) {
@@ -639,11 +651,15 @@ struct WarpDedup {
     unsigned long long val = 0;
   };
 
-  // Publish this warp's pending slots (all lanes call it together).
+  // Publish this warp's pending slots (all lanes call it together). Every
+  // lane stored part of each claimed row; the warp barrier orders those
+  // stores before the fence, and the fence before the relaxed slot stores,
+  // so each slot store is a release of its whole row (and of the owner's
+  // provenance words).
   __device__ static void flush(Pending& pend) {
     if (__any_sync(kFull, pend.slot != nullptr)) {
-      fence_acq_rel_gpu();  // every lane: its stored CM words and provenance first
       __syncwarp();
+      fence_acq_rel_gpu();
       if (pend.slot) st_relaxed(pend.slot, pend.val);
       pend.slot = nullptr;
     }
@@ -761,7 +777,7 @@ struct PathC {
       bool need = false;
       if (state == kProbing) {
         // One atomic per probe: claims an empty slot, or returns what is there.
-        const unsigned long long sv = atomicCAS(cv.table + pos, 0ull, tag | kSlotPending);
+        const unsigned long long sv = cas_acquire(cv.table + pos, 0ull, tag | kSlotPending);
         if (sv == 0ull) {
           state = kClaimed;
         } else {
@@ -775,6 +791,7 @@ struct PathC {
         }
       }
       uint32_t cm = __ballot_sync(kFull, need);
+      if (cm) __syncwarp();  // the probing lanes' acquires, before every lane's row reads
       while (cm) {
         const uint32_t grp = first_bits(cm);
         cm ^= grp;
@@ -1210,7 +1227,7 @@ struct PathD {
     while (true) {
       bool need = false;
       if (state == kProbing) {
-        const unsigned long long sv = atomicCAS(cv.table + pos, 0ull, tag | kSlotPending);
+        const unsigned long long sv = cas_acquire(cv.table + pos, 0ull, tag | kSlotPending);
         if (sv == 0ull) {
           state = kClaimed;
         } else {
@@ -1223,7 +1240,9 @@ struct PathD {
           }
         }
       }
-      for (uint32_t m = __ballot_sync(kFull, need); m; m &= m - 1u) {
+      const uint32_t need_m = __ballot_sync(kFull, need);
+      if (need_m) __syncwarp();  // the probing lanes' acquires, before every lane's row reads
+      for (uint32_t m = need_m; m; m &= m - 1u) {
         const int q = __ffs(m) - 1;
         const uint32_t id = __shfl_sync(kFull, cmp_id, q);
         const uint4* src = row_ptr(cv, id);  // published: visible in L2, read past L1
@@ -2073,7 +2092,7 @@ struct LaunchC {
     BinaryPlan big = plan, small = plan;
     big.n_splits = small.n_splits = 0;
     big.total_tiles = small.total_tiles = 0;
-    static int occ_b = occupancy_blocks((const void*)k_binary_c<W>, 256, size_t(plan.tile) * 32 * sizeof(uint4) + kStageSmem);
+    static int occ_b = occupancy_blocks((const void*)k_binary_c<W>, 256, size_t(32) * 32 * sizeof(uint4) + kStageSmem);
     static int occ_s = occupancy_blocks((const void*)k_binary_small_c<W>, 256, kUnarySmem);
     unsigned long long chunks = 0;
     for (int i = 0; i < plan.n_splits; ++i) {
@@ -2084,7 +2103,8 @@ struct LaunchC {
     // side when there are fewer chunks than that
     const unsigned long long want_s = 4ull * lc.sms * occ_s * 8ull;
     const unsigned long long per_chunk = chunks >= want_s || chunks == 0 ? 1ull : (want_s + chunks - 1) / chunks;
-    // block tiles of 32 rows, or 16 / 8 when 32 gives too few tiles to fill the GPU
+    // block tiles of 32 rows, or 16 / 8 when 32 gives too few tiles to fill the
+    // GPU; a tile the caller fixed (lsyn_config.tile_rows) is kept as it is
     auto tiles_of = [&](uint32_t t) {
       unsigned long long n = 0;
       for (int i = 0; i < plan.n_splits; ++i) {
@@ -2095,7 +2115,7 @@ struct LaunchC {
       return n;
     };
     uint32_t tile = plan.tile;
-    while (tile > 8u && tiles_of(tile) < 2ull * lc.sms * occ_b) tile /= 2u;
+    while (!plan.tile_fixed && tile > 8u && tiles_of(tile) < 2ull * lc.sms * occ_b) tile /= 2u;
     big.tile = tile;
     for (int i = 0; i < plan.n_splits; ++i) {
       Split sp = plan.s[i];

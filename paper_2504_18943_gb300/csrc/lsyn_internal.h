@@ -115,7 +115,8 @@ constexpr int kMaxSplits = 32;
 struct BinaryPlan {
   int n_splits;
   uint32_t ops;                  // bit 0 and, bit 1 or, bit 2 U(a,b), bit 3 U(b,a)
-  uint32_t tile;                 // rows per tile side (path B)
+  uint32_t tile;                 // rows per tile side (512-byte CMs: k_binary_c)
+  uint32_t tile_fixed;           // 1: keep `tile` at every level (no halving at small levels)
   uint32_t work_slot;            // which DevCounters::work counter to use
   unsigned long long total_tiles;
   unsigned long long total_pairs;

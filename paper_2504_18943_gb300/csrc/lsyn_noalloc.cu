@@ -9,11 +9,17 @@
 // writing into an output buffer the caller provides, and keeps its per-node
 // scratch rows in a file-scope device array instead of allocating them.
 //
-// The scratch array is a fixed 8 MiB per GPU, held by every GPU that loads
-// the library until the process exits. Every call on a device shares it and
-// it keeps the last call's contents; nothing in it needs clearing (every row is
-// written before it is read). Calls that overlap on the GPU (different
-// streams, or different host threads on one device) race on it.
+// The scratch array is a fixed 8 MiB per GPU, held until the process exits.
+// The CUDA runtime loads a library's device code lazily (by default), so the
+// array is reserved on a device when this file's code is first loaded there:
+// the first call on each device does that (it also loads the evaluation
+// kernels), and may allocate and synchronise inside the driver. A caller whose
+// memory manager takes the whole GPU must make that first call, e.g. on a
+// one-node formula, before its manager claims the memory, and before any
+// stream capture. Every call on a device shares the array and it keeps the
+// last call's contents; nothing in it needs clearing (every row is written
+// before it is read). Calls that overlap on the GPU (different streams, or
+// different host threads on one device) race on it.
 #include <cstdint>
 #include <cstring>
 #include <functional>
@@ -38,20 +44,6 @@ struct NodeTable {
 
 std::mutex g_setup_mu;
 void* g_scratch_addr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device, looked up once
-// per device (the symbol's host-side name is not a device address).
-cudaError_t scratch_address(int device, void** out) {
-  std::lock_guard<std::mutex> lock(g_setup_mu);
-  if (!g_scratch_addr[device]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_eval_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_addr[device] = p;
-  }
-  *out = g_scratch_addr[device];
-  return cudaSuccess;
-}
 
 __device__ __forceinline__ uint32_t reverse_bits(uint32_t x) { return __brev(x); }
 __device__ __forceinline__ uint64_t reverse_bits(uint64_t x) { return __brevll(x); }
@@ -83,6 +75,26 @@ __global__ void k_eval_noalloc(const W* atoms, const int32_t* lengths, unsigned 
 }
 
 bool parse_nodes(const char* s, int n_props, std::vector<uint32_t>* out, std::string* err);
+
+// First use on a device (with that device current): load the evaluation
+// kernels and this file's device data there, so that every allocation this
+// entry point causes happens now, then look the scratch array's device address
+// up (the symbol's host-side name is not a device address). Later calls reuse
+// the address.
+cudaError_t scratch_address(int device, void** out) {
+  std::lock_guard<std::mutex> lock(g_setup_mu);
+  if (!g_scratch_addr[device]) {
+    cudaFuncAttributes attr;
+    cudaError_t e = cudaFuncGetAttributes(&attr, k_eval_noalloc<uint32_t>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&attr, k_eval_noalloc<uint64_t>);
+    void* p = nullptr;
+    if (e == cudaSuccess) e = cudaGetSymbolAddress(&p, g_eval_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_addr[device] = p;
+  }
+  *out = g_scratch_addr[device];
+  return cudaSuccess;
+}
 
 }  // namespace
 
@@ -118,6 +130,7 @@ extern "C" lsyn_status lsyn_eval_noalloc(int32_t n_props, int32_t n_traces, int3
   for (size_t i = 0; i < nodes.size(); ++i) table.n[i] = nodes[i];
   const unsigned blocks = (unsigned(n_traces) + 127u) / 128u;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaGetLastError();  // an earlier, unrelated launch error on this thread is not this call's
   if (word_bits == 32)
     k_eval_noalloc<uint32_t><<<blocks, 128, 0, st>>>(static_cast<const uint32_t*>(atom_words), lengths,
                                                     unsigned(n_traces), table, int(nodes.size()),

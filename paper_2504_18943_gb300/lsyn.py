@@ -45,7 +45,8 @@ class lsyn_config(ctypes.Structure):
     _fields_ = [("op_mask", ctypes.c_uint32), ("cache_bytes", ctypes.c_uint64), ("table_load", ctypes.c_float),
                 ("full_levels", ctypes.c_int32), ("timing", ctypes.c_int32), ("alloc", ALLOC_FN),
                 ("free", FREE_FN), ("alloc_user", ctypes.c_void_p), ("stream", ctypes.c_void_p),
-                ("device", ctypes.c_int32)]
+                ("device", ctypes.c_int32), ("tile_rows", ctypes.c_int32), ("defer_cap", ctypes.c_uint32),
+                ("hole_cap", ctypes.c_uint32), ("time_limit_ms", ctypes.c_double)]
 
 
 class lsyn_level_stats(ctypes.Structure):
@@ -279,7 +280,8 @@ def pack_problem(problem) -> PackedProblem:
 
 
 def make_config(op_mask: int = 0, cache_bytes: int = 0, table_load: float = 0.0, full_levels: bool = False,
-                timing: bool = False, stream=None, device: int = -1, allocator=None) -> lsyn_config:
+                timing: bool = False, stream=None, device: int = -1, allocator=None, tile_rows: int = 0,
+                defer_cap: int = 0, hole_cap: int = 0, time_limit_ms: float = 0.0) -> lsyn_config:
     cfg = lsyn_config()
     cfg.op_mask = op_mask
     cfg.cache_bytes = cache_bytes
@@ -288,6 +290,10 @@ def make_config(op_mask: int = 0, cache_bytes: int = 0, table_load: float = 0.0,
     cfg.timing = 1 if timing else 0
     cfg.stream = stream
     cfg.device = device
+    cfg.tile_rows = tile_rows
+    cfg.defer_cap = defer_cap
+    cfg.hole_cap = hole_cap
+    cfg.time_limit_ms = time_limit_ms
     if allocator is not None:
         cfg.alloc, cfg.free = allocator.alloc_fn, allocator.free_fn
     else:
@@ -321,13 +327,15 @@ class TorchAllocator:
 
 
 def torch_config(op_mask: int = 0, cache_bytes: int = 0, full_levels: bool = False, timing: bool = False,
-                 stream=None, device: Optional[int] = None, table_load: float = 0.0) -> lsyn_config:
-    """A config whose device memory comes from PyTorch and whose work goes on a torch stream."""
+                 stream=None, device: Optional[int] = None, table_load: float = 0.0, **knobs) -> lsyn_config:
+    """A config whose device memory comes from PyTorch and whose work goes on a
+    torch stream; ``knobs`` are make_config's tile_rows, defer_cap, hole_cap
+    and time_limit_ms."""
     import torch
     dev = torch.cuda.current_device() if device is None else device
     s = stream if stream is not None else torch.cuda.current_stream(dev)
     alloc = TorchAllocator(dev, s)
-    cfg = make_config(op_mask, cache_bytes, table_load, full_levels, timing, s.cuda_stream, dev, alloc)
+    cfg = make_config(op_mask, cache_bytes, table_load, full_levels, timing, s.cuda_stream, dev, alloc, **knobs)
     cfg._torch_stream = s
     return cfg
 
@@ -388,7 +396,7 @@ def lsyn_enumerate_level(ctx, k: int) -> lsyn_level_stats:
 
 def lsyn_solve(ctx, max_size: int, formula_cap: int = 1 << 16):
     """Returns (status, lsyn_result, formula text or None, per-level stats of
-    the levels this call built); LSYN_NOT_FOUND and LSYN_E_CACHE_FULL are
+    the levels this call built); LSYN_NOT_FOUND, LSYN_E_CACHE_FULL and LSYN_E_TIMEOUT are
     results, not exceptions."""
     buf = ctypes.create_string_buffer(formula_cap)
     levels = (lsyn_level_stats * 64)()
@@ -398,7 +406,7 @@ def lsyn_solve(ctx, max_size: int, formula_cap: int = 1 << 16):
     res.level_stats = ctypes.cast(levels, ctypes.POINTER(lsyn_level_stats))
     res.level_stats_cap = 64
     st = _check(_lib.lsyn_solve(ctx, max_size, ctypes.byref(res)), ctx,
-                ok=(LSYN_OK, LSYN_NOT_FOUND, LSYN_E_CACHE_FULL))
+                ok=(LSYN_OK, LSYN_NOT_FOUND, LSYN_E_CACHE_FULL, LSYN_E_TIMEOUT))
     text = buf.value.decode() if st == LSYN_OK else None
     built = [levels[i] for i in range(min(64, res.levels_done)) if levels[i].level == i + 1]
     return st, res, text, built

@@ -35,6 +35,40 @@ def oracle_rows(cms, word_bits: int, n_traces: int, planes: int = 1) -> np.ndarr
     return out[:, :, 0] if planes == 1 else out
 
 
+def oracle_level_words(run, k: int, lengths, word_bits: int, planes: int = 1, chunk: int = 1 << 15) -> np.ndarray:
+    """Level k of an oracle run as words, like oracle_rows, for large levels:
+    the oracle's '0'/'1' rows are exported in bulk and packed with numpy."""
+    lengths = np.asarray(lengths, dtype=np.int64)
+    T = len(lengths)
+    width = planes * word_bits
+    stride = int(lengths.sum()) + T
+    off = np.concatenate([[0], np.cumsum(lengths + 1)[:-1]])  # where trace i's sequence starts
+    t = np.arange(width)
+    idx = np.where(t[None, :] < lengths[:, None], off[:, None] + t[None, :], stride)  # past the end: a '0'
+    dt = np.dtype("<u4") if word_bits == 32 else np.dtype("<u8")
+    n = run.size(k)
+    out = np.empty((n, T, planes), dtype=dt)
+    for first in range(0, n, chunk):
+        c = min(chunk, n - first)
+        text = run.cm_rows(k, first, c)
+        text = np.concatenate([text, np.full((c, 1), ord("0"), dtype=np.uint8)], axis=1)
+        bits = text[:, idx] == ord("1")                            # [c, T, width], position t at index t
+        out[first:first + c] = np.packbits(bits, axis=2, bitorder="little").view(dt)
+    out = out.astype(np.uint32 if word_bits == 32 else np.uint64, copy=False)
+    return out[:, :, 0] if planes == 1 else out
+
+
+def sorted_rows(rows: np.ndarray) -> np.ndarray:
+    """Rows as one opaque byte string each, sorted: equal multisets of rows give
+    equal arrays, and a duplicate row shows up as two equal neighbours."""
+    a = np.ascontiguousarray(rows.reshape(rows.shape[0], -1))
+    return np.sort(a.view(np.dtype((np.void, a.shape[1] * a.itemsize))).ravel())
+
+
+def has_duplicates(srt: np.ndarray) -> bool:
+    return bool(srt.shape[0] > 1 and np.any(srt[1:] == srt[:-1]))
+
+
 def planes_of(problem) -> int:
     """Words per trace of a workloads.Problem."""
     return max(1, -(-int(np.max(problem.traces.lengths)) // problem.word_bits))

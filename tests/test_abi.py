@@ -142,3 +142,40 @@ def test_server_create_fails_cleanly_without_a_gpu(L):
     with pytest.raises(L.LsynError) as ei:
         L.lsyn_server_create(L.make_config(cache_bytes=1 << 26))
     assert ei.value.status < 0
+
+
+def test_binding_structs_match_the_header_layout(L, tmp_path):
+    """Every ctypes struct of the binding has the size and field offsets the C
+    compiler gives the header's struct (compiled with gcc, no GPU)."""
+    structs = {"lsyn_problem": L.lsyn_problem, "lsyn_config": L.lsyn_config,
+               "lsyn_level_stats": L.lsyn_level_stats, "lsyn_result": L.lsyn_result,
+               "lsyn_batch_tuning": L.lsyn_batch_tuning, "lsyn_sched_stats": L.lsyn_sched_stats,
+               "lsyn_step_trace": L.lsyn_step_trace, "lsyn_dc_stats": L.lsyn_dc_stats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lsyn.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} :sizeof %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'  printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(ln.split()[:2]): int(ln.split()[2]) for ln in out if ln.strip()}
+    for name, cls in structs.items():
+        assert got[(name, ":sizeof")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)
+
+
+@pytest.mark.parametrize("knobs", [{"tile_rows": 12}, {"tile_rows": 64}, {"time_limit_ms": -1.0}])
+def test_config_knobs_out_of_range_rejected_before_any_device_call(L, knobs):
+    import oracle
+    from paper_2504_18943_gb300 import workloads as W
+    p = L.pack_problem(W.tiny_problem(0, oracle.labeller))
+    with pytest.raises(L.LsynError) as ei:
+        L.lsyn_create(p, L.make_config(**knobs))
+    assert ei.value.status == L.LSYN_E_INVAL
+    assert "tile_rows" in L.lsyn_last_error() or "time_limit" in L.lsyn_last_error()

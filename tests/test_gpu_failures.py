@@ -1,0 +1,143 @@
+"""Failure paths of the C ABI, made on the host (needs a GPU for the contexts).
+
+No test here faults or hangs the GPU: allocation failures come from a fake
+allocator that returns NULL, overflows from capacities set below what a level
+needs, and timeouts from a deadline that has already passed. Each failure must
+come back as its documented status, release what was allocated, and leave the
+library usable (a reset context, or a new one, gives the oracle's answer)."""
+import pytest
+
+import oracle
+from paper_2504_18943_gb300 import workloads as W
+from tests.gpu_util import lib
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    return lib()
+
+
+class FailingAllocator:
+    """Device memory from torch for the first `budget` requests, then NULL;
+    counts what the library still holds."""
+
+    def __init__(self, L, budget):
+        import torch
+        self.budget, self.calls, self.live = budget, 0, {}
+
+        def _alloc(nbytes, _user):
+            self.calls += 1
+            if self.calls > self.budget:
+                return None
+            t = torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device="cuda")
+            self.live[t.data_ptr()] = t
+            return t.data_ptr()
+
+        def _free(ptr, _user):
+            self.live.pop(ptr, None)
+
+        self.alloc_fn = L.ALLOC_FN(_alloc)
+        self.free_fn = L.FREE_FN(_free)
+
+
+def test_allocator_returning_null_gives_nomem_and_frees_everything(L):
+    p = L.pack_problem(W.tiny_problem(2, oracle.labeller))
+    full = FailingAllocator(L, 1 << 30)
+    with L.Synthesizer(p, L.make_config(cache_bytes=16 << 20, allocator=full)):
+        needed = full.calls
+    assert not full.live and needed > 3
+    for budget in range(needed):
+        a = FailingAllocator(L, budget)
+        with pytest.raises(L.LsynError) as ei:
+            L.lsyn_create(p, L.make_config(cache_bytes=16 << 20, allocator=a))
+        assert ei.value.status == L.LSYN_E_NOMEM, (budget, ei.value)
+        assert not a.live, f"{len(a.live)} allocations left behind after failing at request {budget + 1}"
+    # the library is still usable
+    spec = oracle.Spec.from_problem(W.tiny_problem(2, oracle.labeller))
+    with L.Synthesizer(p, L.make_config(cache_bytes=16 << 20)) as s:
+        st, res, f, _ = s.solve(8)
+    assert st == L.LSYN_OK and res.size == spec.solve(8)[0]
+
+
+def test_scheduler_allocator_returning_null_gives_nomem(L):
+    p = L.pack_problem(W.tiny_problem(2, oracle.labeller))
+    for budget in (0, 3):
+        a = FailingAllocator(L, budget)
+        with pytest.raises(L.LsynError) as ei:
+            L.Batch([p], L.make_config(cache_bytes=16 << 20, allocator=a))
+        assert ei.value.status == L.LSYN_E_NOMEM
+        assert not a.live
+
+
+def test_scheduler_job_that_cannot_fit_answers_nomem(L):
+    """A pool of a few MiB cannot hold a problem whose 64 KiB matrices need
+    more than that for their first level: that job answers LSYN_E_NOMEM, the
+    batch itself succeeds and a small problem beside it is answered."""
+    big = W.labelled_problem("big", 3, 32, 2000, 2000, 30, 60, 5, 64, oracle.labeller)
+    small = W.tiny_problem(7, oracle.labeller)
+    tun = L.make_tuning(pool_bytes=4 << 20)
+    with L.Batch([L.pack_problem(big), L.pack_problem(small)], L.make_config(cache_bytes=1 << 30), tun) as b:
+        statuses, results, formulas = b.solve(8)
+    assert statuses[0] == L.LSYN_E_NOMEM, statuses
+    spec = oracle.Spec.from_problem(small)
+    assert statuses[1] == L.LSYN_OK and results[1].size == spec.solve(8)[0] and spec.separates(formulas[1])
+
+
+def _levels_until_error(s, depth):
+    for k in range(1, depth + 1):
+        try:
+            st = s.level(k)
+        except Exception as e:  # noqa: BLE001
+            return k, e, None
+        last = st
+    return None, None, last
+
+
+def test_hole_log_overflow_is_reported_and_reset_recovers(L):
+    """A one-entry hole log overflows once many warps leave reserved ids
+    unused: the level fails with LSYN_E_STATE; after lsyn_reset the context
+    builds levels again, equal to a fresh context's."""
+    p = W.mid_problem(2, oracle.labeller)
+    packed = L.pack_problem(p)
+    with L.Synthesizer(packed, L.torch_config(cache_bytes=4 << 30, full_levels=True)) as ref:
+        want = [ref.level(k).unique for k in range(1, 4)]
+    with L.Synthesizer(packed, L.torch_config(cache_bytes=4 << 30, full_levels=True, hole_cap=1)) as s:
+        k, err, _ = _levels_until_error(s, 9)
+        assert k is not None, "a one-entry hole log did not overflow by level 9"
+        assert err.status == L.LSYN_E_STATE and "hole" in str(err), err
+        s.reset()
+        assert [s.level(k).unique for k in range(1, 4)] == want
+
+
+def test_deferred_list_overflow_is_reported(L):
+    """With room for one deferred candidate, a level that defers more must
+    fail as not exact instead of dropping candidates."""
+    p = W.mid_problem(2, oracle.labeller)
+    with L.Synthesizer(L.pack_problem(p), L.torch_config(cache_bytes=4 << 30, full_levels=True, defer_cap=1)) as s:
+        k, err, last = _levels_until_error(s, 9)
+    if k is None:
+        assert last.deferred <= 1
+        pytest.skip("no level deferred more than one candidate in this run")
+    assert err.status == L.LSYN_E_STATE and "deferred" in str(err), err
+
+
+def test_time_limit_stops_between_levels_and_solving_continues(L):
+    p = W.mid_problem(1, oracle.labeller)
+    packed = L.pack_problem(p)
+    with L.Synthesizer(packed, L.make_config(cache_bytes=4 << 30)) as ref:
+        st0, r0, f0, _ = ref.solve(12)
+    assert st0 == L.LSYN_OK
+    with L.Synthesizer(packed, L.make_config(cache_bytes=4 << 30, time_limit_ms=1e-6)) as s:
+        calls = 0
+        while True:
+            st, res, f, built = s.solve(12)
+            calls += 1
+            if st != L.LSYN_E_TIMEOUT:
+                break
+            assert len(built) == 1 and res.levels_done == calls, (calls, res.levels_done)
+            assert "time limit" in L.lsyn_last_error(s.ctx)
+    assert st == L.LSYN_OK and res.size == r0.size and calls == r0.size
+    spec = oracle.Spec.from_problem(p)
+    assert spec.separates(f) and W.formula_size(f) == res.size

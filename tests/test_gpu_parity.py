@@ -8,7 +8,8 @@ import pytest
 
 import oracle
 from paper_2504_18943_gb300 import workloads as W
-from tests.gpu_util import assert_levels_match, canon, lib, oracle_rows
+from tests.gpu_util import (assert_levels_match, canon, has_duplicates, lib, oracle_level_words, oracle_rows,
+                            sorted_rows)
 from tests.pins import GOLDEN
 
 pytestmark = pytest.mark.gpu
@@ -178,6 +179,71 @@ def test_mid_solve_full_size(L, seed):
                 f_k = s.formula(k, int(idx))
                 cm = oracle_rows([spec.eval(f_k)], 32, p.n_traces)[0]
                 assert np.array_equal(cm, s.export(k, int(idx), 1)[0]) and W.formula_size(f_k) == k
+
+
+MID_FULL_DEPTH = 8  # the deepest level of the mid workload the oracle builds in about a minute
+
+
+@pytest.fixture(scope="module")
+def mid_oracle():
+    """The benchmark's problem (mid workload, seed 2): the oracle's levels
+    1..8 as sorted rows, and the oracle's own solve up to size 8, run on a
+    second thread meanwhile (the oracle's calls release the interpreter)."""
+    import threading
+    p = W.mid_problem(2, oracle.labeller)
+    spec = oracle.Spec.from_problem(p)
+    solved = {}
+    th = threading.Thread(target=lambda: solved.setdefault("r", spec.solve(MID_FULL_DEPTH)))
+    th.start()
+    run = spec.enumerate(MID_FULL_DEPTH)
+    levels = {k: sorted_rows(oracle_level_words(run, k, p.traces.lengths, 32)) for k in range(1, MID_FULL_DEPTH + 1)}
+    del run  # about 9 GB of strings
+    th.join()
+    return p, spec, levels, solved["r"][0]
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_mid_levels_full_size_each_tile(L, mid_oracle, tile):
+    """Levels 1..8 of the benchmark's problem in its timed configuration
+    (64 GiB cache, torch allocator and stream) equal the oracle's as sets,
+    element by element, with the binary launch's block tile forced to 8, 16
+    and 32 rows. Automatic tiling uses 8- and 16-row tiles at these levels and
+    32-row tiles from level 10, so each tile size the benchmark times is
+    compared whole; levels 7 and 8 (110 k and 685 k entries) also run the
+    deferred passes and the hole close at scale."""
+    p, _, levels, _ = mid_oracle
+    cfg = L.torch_config(cache_bytes=64 << 30, full_levels=True, tile_rows=tile)
+    deferred = 0
+    with L.Synthesizer(L.pack_problem(p), cfg) as s:
+        for k in range(1, MID_FULL_DEPTH + 1):
+            st = s.level(k)
+            assert not st.cache_full and st.unique == levels[k].shape[0], (k, st.unique, levels[k].shape[0])
+            got = sorted_rows(s.export(k))
+            assert not has_duplicates(got), f"duplicate CMs inside level {k} (tile {tile})"
+            assert np.array_equal(got, levels[k]), f"level {k} differs from the oracle (tile {tile})"
+            deferred += st.deferred
+    print(f"tile {tile}: {deferred} candidates deferred over levels 1..{MID_FULL_DEPTH}")
+
+
+@pytest.mark.parametrize("tile", [0, 8, 16, 32])
+def test_mid_solve_full_size_each_tile(L, mid_oracle, tile):
+    """The timed solve (64 GiB cache, early exit) with each tile: the oracle
+    finds no separating formula up to size 8; the GPU's answer separates, has
+    its reported size, lies above 8 and at most at the hidden formula's size,
+    and is the same size for every tile."""
+    p, spec, _, oracle_min = mid_oracle
+    assert oracle_min == 0, "the oracle finds a separating formula of size <= 8"
+    with L.Synthesizer(L.pack_problem(p), L.torch_config(cache_bytes=64 << 30, tile_rows=tile)) as s:
+        st, res, f, _ = s.solve(16)
+    assert st == L.LSYN_OK
+    assert spec.separates(f) and W.formula_size(f) == res.size
+    assert MID_FULL_DEPTH < res.size <= W.formula_size(p.hidden)
+    sizes = test_mid_solve_full_size_each_tile.sizes
+    sizes[tile] = res.size
+    assert len(set(sizes.values())) == 1, sizes
+
+
+test_mid_solve_full_size_each_tile.sizes = {}
 
 
 def _edge(name, pos, neg, props, word_bits=32):
