@@ -311,6 +311,14 @@ typedef struct {
                                lane with the one-problem kernels, beside the batch steps (0 = 2^19) */
   int32_t light_sms;      /* SMs the batch steps keep while a large level runs (0 = 1/8 of the SMs) */
   int32_t lanes;          /* large levels of different problems in flight at once (0 = 4) */
+  int32_t rows_per_item;  /* formulas per warp: rows of the unary work and pairs of the binary work in
+                             one work item of a batch step, each with its 4 operators (2, 4 or 8; 0 = 8) */
+  int32_t words_per_thread; /* CMs above 128 bytes: 16-byte vectors a lane loads together in each step
+                             of its loops over a CM (1 or 2; 0 = 1) */
+  int32_t table_load_pct; /* load, in percent (25..90), up to which a problem's hash table fills before
+                             it is rebuilt larger (0 = the config's table_load). Only the table's size
+                             follows it: the problem's entry limit stays the one lsyn_create derives
+                             from cache_bytes and table_load, so answers do not change. */
 } lsyn_batch_tuning;
 
 typedef struct {
@@ -371,10 +379,12 @@ lsyn_status lsyn_batch_solve(lsyn_batch* batch, int32_t max_size, lsyn_result* r
 
 /*
  * Autotuner: solves the batch (up to max_size) repeatedly, one parameter at a
- * time over blocks per SM {2, 4, 8}, step graphs {off, on}, solo_candidates
- * {2^17, 2^19, 2^21} and light_sms {1/16, 1/8, 1/4 of the SMs}, keeping the
- * fastest value of each; the result serves later lsyn_batch_solve calls and
- * is written to *out (may be NULL).
+ * time over formulas per warp (rows_per_item {2, 4, 8}), words per thread
+ * {1, 2}, table sizing (table_load_pct {25, 50, 75}), blocks per SM {2, 4, 8},
+ * step graphs {off, on}, solo_candidates {2^17, 2^19, 2^21} and light_sms
+ * {1/16, 1/8, 1/4 of the batch's device's SMs}, keeping the fastest value of
+ * each (coordinate descent); the result serves later lsyn_batch_solve calls
+ * and is written to *out (may be NULL). No tuning point changes an answer.
  */
 lsyn_status lsyn_batch_autotune(lsyn_batch* batch, int32_t max_size, lsyn_batch_tuning* out);
 

@@ -37,7 +37,7 @@ def build(force: bool = False) -> str:
     if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    subprocess.run(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-o", tmp, _SRC], check=True)
+    subprocess.run(["g++", "-O2", "-std=c++17", "-pthread", "-shared", "-fPIC", "-o", tmp, _SRC], check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -71,6 +71,8 @@ def _configure(lib) -> None:
     for name in ("oracle_enumerate", "oracle_bruteforce"):
         getattr(lib, name).restype = vp
         getattr(lib, name).argtypes = [vp, i32, ctypes.c_uint]
+    lib.oracle_enumerate_threads.restype = vp
+    lib.oracle_enumerate_threads.argtypes = [vp, i32, ctypes.c_uint, i32]
     lib.oracle_run_free.argtypes = [vp]
     lib.oracle_run_levels.restype = i32
     lib.oracle_run_levels.argtypes = [vp]
@@ -146,6 +148,11 @@ class Spec:
 
     def enumerate(self, max_level: int, op_mask: int = ALL_OPS) -> "Run":
         return Run(self, self._lib.oracle_enumerate(self._h, max_level, op_mask))
+
+    def enumerate_threads(self, max_level: int, threads: int, op_mask: int = ALL_OPS) -> "Run":
+        """The levels of ``enumerate``, each level's candidates shared out among
+        ``threads`` host threads (same sets; entry order may differ)."""
+        return Run(self, self._lib.oracle_enumerate_threads(self._h, max_level, op_mask, threads))
 
     def bruteforce(self, max_size: int, op_mask: int = ALL_OPS) -> "Run":
         return Run(self, self._lib.oracle_bruteforce(self._h, max_size, op_mask))

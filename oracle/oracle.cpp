@@ -45,6 +45,7 @@
 #include <map>
 #include <set>
 #include <string>
+#include <thread>
 #include <vector>
 
 namespace {
@@ -369,6 +370,85 @@ void enumerate(const Spec& s, int max_level, unsigned mask, bool stop_at_solutio
   }
 }
 
+// The levels of enumerate() without the early return, with each level's
+// candidates shared out among `threads` host threads (the CPU baseline on all
+// cores). The candidates are the listing's: every operator, every split,
+// every left and right program; item n of a level (an operator, the left
+// program's size and index) goes to thread n mod threads. Each thread keeps the
+// new characteristic matrices it meets in a set of its own, the cache of the
+// levels below is only read meanwhile, and once every thread is done the sets
+// are merged in thread order. A level is therefore the same set as in
+// enumerate(); only the order of its entries, and so which of several formulas
+// with one characteristic matrix is kept, may differ.
+void enumerate_threads(const Spec& s, int max_level, unsigned mask, int threads, Run* r) {
+  if (threads < 1) threads = 1;
+  r->levels.assign(2, {});
+  r->candidates.assign(2, 0);
+  std::set<std::string> cache;
+  for (int p = 0; p < s.n_props; ++p) {
+    Entry e;
+    e.op = ATOM; e.prop = p; e.la = e.ia = e.lb = e.ib = -1;
+    for (const Trace& tr : s.traces) e.cm.push_back(seq_atom(tr, p));
+    r->candidates[1] += 1;
+    r->constructed += 1;
+    if (cache.insert(join(e.cm)).second) r->levels[1].push_back(std::move(e));
+  }
+  const int kOps[7] = {NOT, AND, OR, NEXT, FUTURE, GLOBALLY, UNTIL};
+  struct Item { int op, i, x; };
+  for (int size = 2; size <= max_level; ++size) {
+    r->levels.emplace_back();
+    r->candidates.push_back(0);
+    std::vector<Item> items;
+    for (int op : kOps) {
+      if (!enabled(mask, op)) continue;
+      if (!is_binary(op)) {
+        for (int x = 0; x < (int)r->levels[size - 1].size(); ++x) items.push_back({op, size - 1, x});
+        continue;
+      }
+      for (int i = 1; i <= size - 2; ++i)
+        for (int x = 0; x < (int)r->levels[i].size(); ++x) items.push_back({op, i, x});
+    }
+    std::vector<std::map<std::string, Entry>> found(threads);
+    std::vector<int64_t> built(threads, 0);
+    auto work = [&](int t) {
+      for (size_t n = t; n < items.size(); n += threads) {
+        const Item& it = items[n];
+        const CM& a = r->levels[it.i][it.x].cm;
+        auto consider = [&](Entry&& e) {
+          built[t] += 1;
+          std::string key = join(e.cm);
+          if (!cache.count(key)) found[t].emplace(std::move(key), std::move(e));  // the first one found stays
+        };
+        if (!is_binary(it.op)) {
+          Entry e;
+          e.op = it.op; e.prop = 0; e.la = it.i; e.ia = it.x; e.lb = -1; e.ib = -1;
+          for (const std::string& seq : a) e.cm.push_back(seq_unary(it.op, seq));
+          consider(std::move(e));
+          continue;
+        }
+        const int j = size - 1 - it.i;
+        for (int y = 0; y < (int)r->levels[j].size(); ++y) {
+          const CM& b = r->levels[j][y].cm;
+          Entry e;
+          e.op = it.op; e.prop = 0; e.la = it.i; e.ia = it.x; e.lb = j; e.ib = y;
+          for (size_t k = 0; k < a.size(); ++k) e.cm.push_back(seq_binary(it.op, a[k], b[k]));
+          consider(std::move(e));
+        }
+      }
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < threads; ++t) pool.emplace_back(work, t);
+    work(0);
+    for (std::thread& th : pool) th.join();
+    for (int t = 0; t < threads; ++t) {
+      r->candidates[size] += built[t];
+      r->constructed += built[t];
+      for (auto& kv : found[t])
+        if (cache.insert(kv.first).second) r->levels[size].push_back(std::move(kv.second));
+    }
+  }
+}
+
 // All syntax trees of an exact size, as texts (no deduplication of any kind).
 void trees_of_size(int size, int n_props, unsigned mask, std::vector<std::vector<std::string>>* memo) {
   if ((int)memo->size() > size && !(*memo)[size].empty()) return;
@@ -500,6 +580,13 @@ int oracle_separates(const void* spec, const char* formula) {
 void* oracle_enumerate(const void* spec, int max_level, unsigned op_mask) {
   Run* r = new Run;
   enumerate(*static_cast<const Spec*>(spec), max_level, op_mask, false, r);
+  return r;
+}
+
+// The same levels, each level's candidates shared out among `threads` threads.
+void* oracle_enumerate_threads(const void* spec, int max_level, unsigned op_mask, int threads) {
+  Run* r = new Run;
+  enumerate_threads(*static_cast<const Spec*>(spec), max_level, op_mask, threads, r);
   return r;
 }
 

@@ -187,23 +187,38 @@ lsyn_status lsyn_batch_autotune(lsyn_batch* b, int32_t max_size, lsyn_batch_tuni
   lsyn_batch_tuning best = saved;
   double best_ms = 1e300;
   if ((s = time_it(best, &best_ms)) != LSYN_OK) return s;
-  int sms = 1;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
-  // coordinate descent: one parameter at a time, keep the fastest value
+  const int sms = b->eng.sm_count();  // of the batch's device
+  // Coordinate descent: one parameter at a time, keep the fastest value. The
+  // first three axes are the kernel's shape: formulas per warp (rows / pairs
+  // per work item), words per thread (vectors a lane loads together on CMs
+  // above 128 bytes) and table sizing (the load up to which tables fill);
+  // then the launch: blocks per SM, graph replay, the large-level threshold
+  // and the SMs kept for batch steps.
+  const int32_t rows[3] = {2, 4, 8};
+  const int32_t wpt[2] = {1, 2};
+  const int32_t load_pct[3] = {25, 50, 75};
   const int32_t blocks[3] = {2, 4, 8};
   const uint64_t solo[3] = {1ull << 17, 1ull << 19, 1ull << 21};
   const int32_t light[3] = {std::max(1, sms / 16), std::max(1, sms / 8), std::max(1, sms / 4)};
-  for (int axis = 0; axis < 4; ++axis) {
+  for (int axis = 0; axis < 7; ++axis) {
     std::vector<lsyn_batch_tuning> cand;
     for (int v = 0; v < 3; ++v) {
       lsyn_batch_tuning t = best;
-      if (axis == 0) t.blocks_per_sm = blocks[v];
-      if (axis == 1) {
-        if (v == 2) continue;
-        t.use_graph = v;
+      switch (axis) {
+        case 0: t.rows_per_item = rows[v]; break;
+        case 1:
+          if (v == 2) continue;
+          t.words_per_thread = wpt[v];
+          break;
+        case 2: t.table_load_pct = load_pct[v]; break;
+        case 3: t.blocks_per_sm = blocks[v]; break;
+        case 4:
+          if (v == 2) continue;
+          t.use_graph = v;
+          break;
+        case 5: t.solo_candidates = solo[v]; break;
+        default: t.light_sms = light[v]; break;
       }
-      if (axis == 2) t.solo_candidates = solo[v];
-      if (axis == 3) t.light_sms = light[v];
       cand.push_back(t);
     }
     for (const lsyn_batch_tuning& t : cand) {

@@ -1167,13 +1167,29 @@ __global__ void __launch_bounds__(256, 4) k_desc_c(CacheView cv, const unsigned 
 // ===========================================================================
 // Path D (CMs above 512 bytes, e.g. 2048 traces of 64-bit words = 16 KiB): the
 // hash-first scheme of path C with rv = vecs / 32 vectors per lane, walked in
-// loops. Operand rows are read through L1/L2 whenever a candidate is
-// (re)computed; compares read the stored row directly.
+// loops, VPT vectors at a time (their operand loads in flight together).
+// Operand rows are read through L1/L2 whenever a candidate is (re)computed;
+// compares read the stored row directly.
 // ===========================================================================
-template <typename W>
+template <typename W, int VPT = 1>
 struct PathD {
   using Pending = WarpDedup::Pending;
   using Ids = WarpDedup::Ids;
+
+  // f(v, c) for this lane's vectors v of candidate q, VPT computed together.
+  template <class Gen, class F>
+  __device__ static void each_vec(const Gen& gen, int q, unsigned rv, F&& f) {
+    const unsigned lane = threadIdx.x & 31u;
+    for (unsigned r = 0; r < rv; r += VPT) {
+      uint4 c[VPT];
+#pragma unroll
+      for (int u = 0; u < VPT; ++u)
+        c[u] = r + u < rv ? gen.compute(q, lane + 32u * (r + u)) : make_uint4(0, 0, 0, 0);
+#pragma unroll
+      for (int u = 0; u < VPT; ++u)
+        if (r + u < rv) f(lane + 32u * (r + u), c[u]);
+    }
+  }
 
   template <bool kEarlyPublish, class Gen>
   __device__ static void batch(const CacheView& cv, const Gen& gen, int n, uint32_t en, Pending& pend, Ids& ids) {
@@ -1184,12 +1200,10 @@ struct PathD {
     for (int q = 0; q < n; ++q) {
       uint64_t acc = 0;
       uint32_t diff = 0;
-      for (unsigned r = 0; r < rv; ++r) {
-        const unsigned v = lane + 32u * r;
-        const uint4 c = gen.compute(q, v);
+      each_vec(gen, q, rv, [&](unsigned v, const uint4& c) {
         acc = h_mac(c, __ldg(cv.hmul + v), acc);
         if (v < cv.plane_vecs) diff |= bit0s<W>(c) ^ bit0s<W>(__ldg(cv.label + v));  // position 0: plane 0
-      }
+      });
       const uint32_t lo = __reduce_add_sync(kFull, uint32_t(acc));
       const uint32_t hi = __reduce_add_sync(kFull, uint32_t(acc >> 32));
       my_lo = lane == q ? lo : my_lo;
@@ -1217,7 +1231,7 @@ struct PathD {
       const int q = __ffs(m) - 1;
       const int p = __shfl_sync(kFull, twin, q);
       uint32_t ne = 0;
-      for (unsigned r = 0; r < rv; ++r) ne |= v_ne(gen.compute(q, lane + 32u * r), gen.compute(p, lane + 32u * r));
+      each_vec(gen, q, rv, [&](unsigned v, const uint4& c) { ne |= v_ne(c, gen.compute(p, v)); });
       const bool eq = !__any_sync(kFull, ne != 0u);
       if (lane == q && eq) state = kDone;
     }
@@ -1247,7 +1261,7 @@ struct PathD {
         const uint32_t id = __shfl_sync(kFull, cmp_id, q);
         const uint4* src = row_ptr(cv, id);  // published: visible in L2, read past L1
         uint32_t ne = 0;
-        for (unsigned r = 0; r < rv; ++r) ne |= v_ne(__ldcg(src + lane + 32u * r), gen.compute(q, lane + 32u * r));
+        each_vec(gen, q, rv, [&](unsigned v, const uint4& c) { ne |= v_ne(__ldcg(src + v), c); });
         const bool eq = !__any_sync(kFull, ne != 0u);
         if (lane == q) {
           if (eq) state = kDone;
@@ -1276,7 +1290,7 @@ struct PathD {
         const unsigned id = rank < have ? ids.next + rank : fresh + (rank - have);
         if (id < cv.max_entries) {
           uint4* dst = cv.arena + size_t(id) * cv.vecs;
-          for (unsigned r = 0; r < rv; ++r) dst[lane + 32u * r] = gen.compute(q, lane + 32u * r);
+          each_vec(gen, q, rv, [&](unsigned v, const uint4& c) { dst[v] = c; });
         }
       }
       const unsigned my_rank = unsigned(__popc(claim & ((1u << lane) - 1u)));
@@ -1555,8 +1569,9 @@ __device__ unsigned batch_a(const CacheView& cv, const uint4* ca, uint64_t d, bo
   return __reduce_add_sync(kFull, ins);
 }
 
-template <typename W>
+template <typename W, int VPT>
 __global__ void __launch_bounds__(256) k_batch_run(StepHeader* hdr, const StepProblem* steps) {
+  using PD = PathD<W, VPT>;
   __shared__ CacheView s_cv[8];
   __shared__ uint2 s_pairs[8][8];
   __shared__ uint64_t s_d[8][32];
@@ -1565,6 +1580,7 @@ __global__ void __launch_bounds__(256) k_batch_run(StepHeader* hdr, const StepPr
   CacheView* cv = &s_cv[wib];
   uint4* ca = s_ca[wib];
   const int n = hdr->n;
+  const uint32_t R = uint32_t(hdr->rows);  // unary rows / binary pairs per work item (2, 4 or 8)
   BatchWarp<W> bw;
   auto enter = [&](int p) {
     const bool fresh = p != bw.cur;
@@ -1588,20 +1604,20 @@ __global__ void __launch_bounds__(256) k_batch_run(StepHeader* hdr, const StepPr
       ListGenD<W> gen;
       gen.cv = cv;
       gen.d = s_d[wib];
-      PathD<W>::template batch<false>(*cv, gen, int(cnt), cnt >= 32u ? 0xFFFFFFFFu : ((1u << cnt) - 1u), bw.pend,
-                                      bw.ids);
+      PD::template batch<false>(*cv, gen, int(cnt), cnt >= 32u ? 0xFFFFFFFFu : ((1u << cnt) - 1u), bw.pend,
+                                bw.ids);
     }
     if (!sp.d_list) bw.built += cnt;  // atoms count as built; deferred ones were counted when first built
     __syncwarp();
   }
-  // 2. unary operators, 8 rows (32 candidates) per item
+  // 2. unary operators, R rows (4R candidates) per item
   for (unsigned long long it = grab(&hdr->work[1].v); it < hdr->total_u; it = grab(&hdr->work[1].v)) {
     const int p = find_problem(steps, n, it, 1);
     enter(p);
     if (__any_sync(kFull, stop_requested(*cv))) continue;
     const StepProblem& sp = steps[p];
-    const uint32_t base = uint32_t(it - sp.u_items_begin) * 8u;
-    const uint32_t nrows = min(8u, sp.u_count - base);
+    const uint32_t base = uint32_t(it - sp.u_items_begin) * R;
+    const uint32_t nrows = min(R, sp.u_count - base);
     uint32_t en = 0;
 #pragma unroll
     for (int q = 0; q < 32; ++q) en |= ((sp.u_ops >> (q & 3)) & 1u & (uint32_t(q >> 2) < nrows ? 1u : 0u)) << q;
@@ -1613,19 +1629,19 @@ __global__ void __launch_bounds__(256) k_batch_run(StepHeader* hdr, const StepPr
       RowGenD<W> gen;
       gen.cv = cv;
       gen.id0 = sp.u_first + base;
-      PathD<W>::template batch<false>(*cv, gen, int(4 * nrows), en, bw.pend, bw.ids);
+      PD::template batch<false>(*cv, gen, int(4 * nrows), en, bw.pend, bw.ids);
     }
     bw.built += __popc(en);
   }
-  // 3. binary operators, 8 pairs (32 candidates) per item
+  // 3. binary operators, R pairs (4R candidates) per item
   for (unsigned long long it = grab(&hdr->work[2].v); it < hdr->total_b; it = grab(&hdr->work[2].v)) {
     const int p = find_problem(steps, n, it, 2);
     enter(p);
     if (__any_sync(kFull, stop_requested(*cv))) continue;
     const StepProblem& sp = steps[p];
-    const unsigned long long g0 = (it - sp.b_items_begin) * 8ull;
+    const unsigned long long g0 = (it - sp.b_items_begin) * (unsigned long long)R;
     uint32_t ok = 0;
-    if (lane < 8) {
+    if (lane < int(R)) {
       unsigned long long pidx = g0 + lane;
       int si = 0;
       while (si + 1 < int(sp.n_splits) && sp.s[si + 1].pairs_begin <= pidx) ++si;
@@ -1657,7 +1673,7 @@ __global__ void __launch_bounds__(256) k_batch_run(StepHeader* hdr, const StepPr
         PairGenD<W> gen;
         gen.cv = cv;
         gen.pairs = s_pairs[wib];
-        PathD<W>::template batch<true>(*cv, gen, 32, en, bw.pend, bw.ids);
+        PD::template batch<true>(*cv, gen, int(4 * R), en, bw.pend, bw.ids);
       }
       bw.built += __popc(en);
     }
@@ -2224,8 +2240,11 @@ cudaError_t Kernels<W>::batch_begin(StepHeader* hdr, const StepProblem* steps, i
 }
 
 template <typename W>
-cudaError_t Kernels<W>::batch_run(StepHeader* hdr, const StepProblem* steps, const LaunchCfg& lc, int blocks_per_sm) {
-  k_batch_run<W><<<unsigned(lc.sms * std::max(1, blocks_per_sm)), 256, 0, lc.stream>>>(hdr, steps);
+cudaError_t Kernels<W>::batch_run(StepHeader* hdr, const StepProblem* steps, const LaunchCfg& lc, int blocks_per_sm,
+                                  int vpt) {
+  const unsigned grid = unsigned(lc.sms * std::max(1, blocks_per_sm));
+  if (vpt >= 2) k_batch_run<W, 2><<<grid, 256, 0, lc.stream>>>(hdr, steps);
+  else k_batch_run<W, 1><<<grid, 256, 0, lc.stream>>>(hdr, steps);
   return cudaGetLastError();
 }
 

@@ -85,6 +85,7 @@ lsyn_status Engine::init(const lsyn_config* cfg, const lsyn_batch_tuning* tune, 
   if (tune) tune_ = *tune;
   if (tune_.blocks_per_sm < 1) tune_.blocks_per_sm = 4;
   if (max_active < 1) { err = "max_active must be positive"; return LSYN_E_INVAL; }
+  if (!valid_tuning(tune_, &err)) return LSYN_E_INVAL;
   tune_.max_active = max_active;
   keep_finished_ = keep_finished;
   cudaError_t e;
@@ -173,6 +174,22 @@ void Engine::drop_graphs() {
   graphs_.clear();
 }
 
+bool Engine::valid_tuning(const lsyn_batch_tuning& t, std::string* e) {
+  if (t.rows_per_item != 0 && t.rows_per_item != 2 && t.rows_per_item != 4 && t.rows_per_item != 8) {
+    *e = "rows_per_item must be 0, 2, 4 or 8";
+    return false;
+  }
+  if (t.words_per_thread < 0 || t.words_per_thread > 2) {
+    *e = "words_per_thread must be 0, 1 or 2";
+    return false;
+  }
+  if (t.table_load_pct != 0 && (t.table_load_pct < 25 || t.table_load_pct > 90)) {
+    *e = "table_load_pct must be 0 or in 25..90";
+    return false;
+  }
+  return true;
+}
+
 void Engine::set_tune(const lsyn_batch_tuning& t) {
   if (stream_) cudaStreamSynchronize(stream_);
   tune_.blocks_per_sm = t.blocks_per_sm > 0 ? t.blocks_per_sm : 4;
@@ -180,6 +197,9 @@ void Engine::set_tune(const lsyn_batch_tuning& t) {
   tune_.predict_pct = t.predict_pct;
   tune_.solo_candidates = t.solo_candidates;
   tune_.light_sms = t.light_sms;  // the number of lane tracks is fixed at creation
+  tune_.rows_per_item = t.rows_per_item;
+  tune_.words_per_thread = t.words_per_thread;
+  tune_.table_load_pct = t.table_load_pct;
   drop_graphs();  // the launch shape is part of each graph
 }
 
@@ -228,7 +248,7 @@ std::vector<lsyn_step_trace> Engine::trace() const {
 bool Engine::reserve_slot(Slot& s, const Job* j, std::string* e) {
   const unsigned long long cap = j->cap_entries + 64;
   const size_t M = size_t(j->c->vecs) * 16;
-  const double load = j->c->table_load;
+  const double load = std::min(j->c->table_load, table_load(j));
   const unsigned long long max_t = std::max(pow2_at_least((unsigned long long)(double(cap) / load) + 2),
                                             (unsigned long long)(pool_.granularity() / 8));
   auto fit = [&](Segment& sg, size_t bytes) {
@@ -486,7 +506,7 @@ size_t Engine::growth_cost(const Job* j, unsigned long long entries) const {
   const size_t dlimit = size_t(defer_cap_for(cap)) * 8;
   add(s.defer[0].grow_cost(pool_, dbytes, dlimit));
   add(s.defer[1].grow_cost(pool_, dbytes, dlimit));
-  const unsigned long long want_t = pow2_at_least((unsigned long long)(double(entries) / c->table_load) + 1);
+  const unsigned long long want_t = pow2_at_least((unsigned long long)(double(entries) / table_load(j)) + 1);
   if (want_t > s.tcap || j->redo) {
     const size_t tb = size_t(std::max(want_t, s.tcap)) * 8;
     add(s.tcap == 0 ? s.table[s.cur_table].grow_cost(pool_, tb) : s.table[1 - s.cur_table].grow_cost(pool_, tb));
@@ -544,7 +564,7 @@ lsyn_status Engine::grow(Job* j, unsigned long long entries, Lane* ln, bool* ok)
       !s.defer[1].grow(pool_, dbytes, &e2, dlimit))
     return LSYN_OK;  // the pool ran short (another size class was needed): try again later
   const unsigned long long live = c->level_start.back() + c->level_n.back();
-  const unsigned long long want_t = pow2_at_least((unsigned long long)(double(entries) / c->table_load) + 1);
+  const unsigned long long want_t = pow2_at_least((unsigned long long)(double(entries) / table_load(j)) + 1);
   if (want_t > s.tcap || j->redo) {
     Segment* old = nullptr;
     lsyn_status r = rebuild_table(j, std::max(want_t, s.tcap), uint32_t(live), st, &old);
@@ -567,7 +587,7 @@ lsyn_status Engine::grow(Job* j, unsigned long long entries, Lane* ln, bool* ok)
   have = std::min<unsigned long long>(have, s.prov.mapped() / 8);
   have = std::min<unsigned long long>(have, s.slotpos.mapped() / 4);
   have = std::min<unsigned long long>(have, s.homes.mapped() / 4);
-  have = std::min<unsigned long long>(have, (unsigned long long)(double(s.tcap) * c->table_load));
+  have = std::min<unsigned long long>(have, (unsigned long long)(double(s.tcap) * table_load(j)));
   c->max_entries = unsigned(have);
   c->defer_cap = unsigned(std::min<size_t>(kDeferMax, std::min(s.defer[0].mapped(), s.defer[1].mapped()) / 8));
   note_peak();
@@ -760,10 +780,10 @@ lsyn_status Engine::launch_step(int word_bits, int n, int sms) {
       cudaMemcpyAsync(d_steps_, h_steps_, sizeof(StepProblem) * size_t(bucket), cudaMemcpyHostToDevice, stream_);
       if (word_bits == 32) {
         Kernels<uint32_t>::batch_begin(d_hdr_, d_steps_, bucket, lc);
-        Kernels<uint32_t>::batch_run(d_hdr_, d_steps_, lc, tune_.blocks_per_sm);
+        Kernels<uint32_t>::batch_run(d_hdr_, d_steps_, lc, tune_.blocks_per_sm, tune_.words_per_thread);
       } else {
         Kernels<uint64_t>::batch_begin(d_hdr_, d_steps_, bucket, lc);
-        Kernels<uint64_t>::batch_run(d_hdr_, d_steps_, lc, tune_.blocks_per_sm);
+        Kernels<uint64_t>::batch_run(d_hdr_, d_steps_, lc, tune_.blocks_per_sm, tune_.words_per_thread);
       }
       cudaMemcpyAsync(h_ctrs_, ctrs_, sizeof(DevCounters) * slots_.size(), cudaMemcpyDeviceToHost, stream_);
       e = cudaStreamEndCapture(stream_, &gr.first);
@@ -781,8 +801,8 @@ lsyn_status Engine::launch_step(int word_bits, int n, int sms) {
       e = word_bits == 32 ? Kernels<uint32_t>::batch_begin(d_hdr_, d_steps_, n, lc)
                           : Kernels<uint64_t>::batch_begin(d_hdr_, d_steps_, n, lc);
     if (e == cudaSuccess)
-      e = word_bits == 32 ? Kernels<uint32_t>::batch_run(d_hdr_, d_steps_, lc, tune_.blocks_per_sm)
-                          : Kernels<uint64_t>::batch_run(d_hdr_, d_steps_, lc, tune_.blocks_per_sm);
+      e = word_bits == 32 ? Kernels<uint32_t>::batch_run(d_hdr_, d_steps_, lc, tune_.blocks_per_sm, tune_.words_per_thread)
+                          : Kernels<uint64_t>::batch_run(d_hdr_, d_steps_, lc, tune_.blocks_per_sm, tune_.words_per_thread);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(h_ctrs_, ctrs_, sizeof(DevCounters) * slots_.size(), cudaMemcpyDeviceToHost, stream_);
     if (e != cudaSuccess) { err = std::string("batch step: ") + cudaGetErrorString(e); return LSYN_E_CUDA; }
@@ -799,8 +819,8 @@ lsyn_status Engine::launch_plain(int word_bits, int n, int sms) {
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d_steps_, h_steps_, sizeof(StepProblem) * size_t(n), cudaMemcpyHostToDevice, stream_);
   if (e == cudaSuccess)
-    e = word_bits == 32 ? Kernels<uint32_t>::batch_run(d_hdr_, d_steps_, lc, tune_.blocks_per_sm)
-                        : Kernels<uint64_t>::batch_run(d_hdr_, d_steps_, lc, tune_.blocks_per_sm);
+    e = word_bits == 32 ? Kernels<uint32_t>::batch_run(d_hdr_, d_steps_, lc, tune_.blocks_per_sm, tune_.words_per_thread)
+                        : Kernels<uint64_t>::batch_run(d_hdr_, d_steps_, lc, tune_.blocks_per_sm, tune_.words_per_thread);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h_ctrs_, ctrs_, sizeof(DevCounters) * slots_.size(), cudaMemcpyDeviceToHost, stream_);
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream_);
@@ -838,6 +858,7 @@ lsyn_status Engine::answer(const std::vector<Job*>& solved) {
 
 lsyn_status Engine::run_group(std::vector<Plan>& g, int word_bits, int sms) {
   const int n = int(g.size());
+  const unsigned R = rows_per_item();
   const unsigned long long warps = (unsigned long long)sms * unsigned(tune_.blocks_per_sm) * 8ull;
   // 1. plan every job's level and pack the step array
   unsigned long long tu = 0, tb = 0, td = 0;
@@ -867,11 +888,11 @@ lsyn_status Engine::run_group(std::vector<Plan>& g, int word_bits, int sms) {
       sp.u_first = p.lp.u_first;
       sp.u_count = p.lp.u_count;
       sp.u_ops = p.lp.uops;
-      tu += (sp.u_count + 7u) / 8u;
+      tu += (sp.u_count + R - 1u) / R;
       sp.b_ops = p.lp.plan.ops;
       sp.n_splits = uint32_t(p.lp.plan.n_splits);
       for (int t = 0; t < p.lp.plan.n_splits; ++t) sp.s[t] = p.lp.plan.s[t];
-      tb += (p.lp.plan.total_pairs + 7ull) / 8ull;
+      tb += (p.lp.plan.total_pairs + R - 1ull) / R;
     }
   }
   memset(h_hdr_, 0, sizeof(StepHeader));
@@ -879,6 +900,7 @@ lsyn_status Engine::run_group(std::vector<Plan>& g, int word_bits, int sms) {
   h_hdr_->total_b = tb;
   h_hdr_->total_d = td;
   h_hdr_->n = n;
+  h_hdr_->rows = int(R);
   const double tr = now_ms();
   lsyn_status s = launch_step(word_bits, n, sms);
   if (s != LSYN_OK) return s;
@@ -920,6 +942,7 @@ lsyn_status Engine::run_group(std::vector<Plan>& g, int word_bits, int sms) {
     memset(h_hdr_, 0, sizeof(StepHeader));
     h_hdr_->total_d = td2;
     h_hdr_->n = int(need.size());
+    h_hdr_->rows = int(R);
     if ((s = launch_plain(word_bits, int(need.size()), sms)) != LSYN_OK) return s;
   }
 

@@ -105,8 +105,13 @@ class Engine {
   void clear();
 
   lsyn_batch_tuning tune() const { return tune_; }
+  // Applies the launch-shape fields of t (not max_active, pool_bytes, lanes);
+  // call between solves, with t checked by valid_tuning.
   void set_tune(const lsyn_batch_tuning& t);
+  static bool valid_tuning(const lsyn_batch_tuning& t, std::string* e);
   const BlockPool& pool() const { return pool_; }
+  int device() const { return device_; }
+  int sm_count() const { return sms_; }
   size_t peak_in_use() const { return peak_; }
   uint64_t steps_run() const { return steps_; }
   uint64_t evictions() const { return evictions_; }
@@ -227,6 +232,12 @@ class Engine {
   void drop_graphs();
   unsigned long long candidates(const Job* j, int k) const;
   unsigned long long solo_min() const { return tune_.solo_candidates ? tune_.solo_candidates : (1ull << 19); }
+  // unary rows / binary pairs per work item of a batch step
+  unsigned rows_per_item() const { return tune_.rows_per_item > 0 ? unsigned(tune_.rows_per_item) : 8u; }
+  // load up to which a job's table fills before it is rebuilt larger (its entry limit does not depend on it)
+  double table_load(const Job* j) const {
+    return tune_.table_load_pct > 0 ? double(tune_.table_load_pct) / 100.0 : j->c->table_load;
+  }
   int light_sms() const;
   unsigned long long predict_entries(const Job* j, int k, unsigned long long cand) const;
   size_t growth_cost(const Job* j, unsigned long long entries) const;

@@ -145,7 +145,8 @@ struct StepProblem {
 struct alignas(128) StepHeader {
   unsigned long long total_u, total_b, total_d;
   int n;                       // problems in this step
-  int pad0[25];
+  int rows;                    // unary rows / binary pairs per work item (2, 4 or 8)
+  int pad0[24];
   struct alignas(128) Counter {
     unsigned long long v;
     unsigned long long pad[15];
@@ -174,7 +175,9 @@ struct Kernels {
   // Batch step (problems at their own levels; all use whole warps of vectors):
   // reset counters, then descriptor (atoms / deferred), unary and binary work.
   static cudaError_t batch_begin(StepHeader* hdr, const StepProblem* steps, int n, const LaunchCfg& lc);
-  static cudaError_t batch_run(StepHeader* hdr, const StepProblem* steps, const LaunchCfg& lc, int blocks_per_sm);
+  // vpt: 16-byte vectors a lane loads together in the loops over a CM above 128 bytes (1 or 2).
+  static cudaError_t batch_run(StepHeader* hdr, const StepProblem* steps, const LaunchCfg& lc, int blocks_per_sm,
+                               int vpt);
   // Moves (problem index, src, dst) of a batch step; then each problem's entry count.
   static cudaError_t batch_fixup(const StepProblem* steps, const uint4* moves, unsigned n, const unsigned* dense_end,
                                  int n_problems, const LaunchCfg& lc);

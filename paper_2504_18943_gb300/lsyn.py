@@ -74,7 +74,9 @@ class lsyn_result(ctypes.Structure):
 class lsyn_batch_tuning(ctypes.Structure):
     _fields_ = [("blocks_per_sm", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("max_active", ctypes.c_int32),
                 ("predict_pct", ctypes.c_int32), ("pool_bytes", ctypes.c_uint64),
-                ("solo_candidates", ctypes.c_uint64), ("light_sms", ctypes.c_int32), ("lanes", ctypes.c_int32)]
+                ("solo_candidates", ctypes.c_uint64), ("light_sms", ctypes.c_int32), ("lanes", ctypes.c_int32),
+                ("rows_per_item", ctypes.c_int32), ("words_per_thread", ctypes.c_int32),
+                ("table_load_pct", ctypes.c_int32)]
 
 
 class lsyn_sched_stats(ctypes.Structure):
@@ -107,11 +109,12 @@ class lsyn_dc_stats(ctypes.Structure):
 
 
 def make_tuning(blocks_per_sm: int = 0, use_graph: int = 0, max_active: int = 0, pool_bytes: int = 0,
-                predict_pct: int = 0, solo_candidates: int = 0, light_sms: int = 0, lanes: int = 0
-                ) -> lsyn_batch_tuning:
+                predict_pct: int = 0, solo_candidates: int = 0, light_sms: int = 0, lanes: int = 0,
+                rows_per_item: int = 0, words_per_thread: int = 0, table_load_pct: int = 0) -> lsyn_batch_tuning:
     t = lsyn_batch_tuning()
     t.blocks_per_sm, t.use_graph, t.max_active, t.pool_bytes = blocks_per_sm, use_graph, max_active, pool_bytes
     t.predict_pct, t.solo_candidates, t.light_sms, t.lanes = predict_pct, solo_candidates, light_sms, lanes
+    t.rows_per_item, t.words_per_thread, t.table_load_pct = rows_per_item, words_per_thread, table_load_pct
     return t
 
 

@@ -76,6 +76,46 @@ def test_batch_graph_and_autotune(L, problems):
         assert g[0] == ref[0]
         assert [r.size for r in g[1]] == [r.size for r in ref[1]]
     assert t.blocks_per_sm in (2, 4, 6, 8) and t.use_graph in (0, 1)
+    assert t.rows_per_item in (2, 4, 8) and t.words_per_thread in (1, 2) and t.table_load_pct in (25, 50, 75)
+
+
+@pytest.mark.parametrize("rows", [2, 4, 8])
+@pytest.mark.parametrize("wpt", [1, 2])
+@pytest.mark.parametrize("load", [25, 75])
+def test_every_tuning_point_gives_the_plain_answers(L, problems, rows, wpt, load):
+    """Each point of the autotuner's kernel axes (formulas per warp, words
+    per thread, table sizing) gives every problem the plain path's status,
+    minimal size and complete levels; small caches make some problems fill
+    theirs, so the entry limit must not move with the table's load."""
+    packed = [L.pack_problem(p) for p in problems[:16]]
+    cfg = L.make_config(cache_bytes=64 << 20)
+    tun = L.make_tuning(rows_per_item=rows, words_per_thread=wpt, table_load_pct=load, use_graph=1)
+    plain = test_every_tuning_point_gives_the_plain_answers.plain
+    if not plain:
+        for q in packed:
+            with L.Synthesizer(q, cfg) as s:
+                st, res, f, _ = s.solve(9)
+                plain.append((st, res.size, res.levels_done,
+                              [canon(s.export(k)) for k in _complete_levels(st, res)]))
+    with L.Batch(packed, cfg, tun) as b:
+        statuses, results, formulas = b.solve(9)
+        for i, (st, size, done, levels) in enumerate(plain):
+            assert statuses[i] == st, (i, statuses[i], st)
+            if st == L.LSYN_OK:
+                assert results[i].size == size
+            for k, want in zip(_complete_levels(st, results[i]), levels):
+                assert np.array_equal(canon(b.export(i, k)), want), (i, k)
+
+
+test_every_tuning_point_gives_the_plain_answers.plain = []
+
+
+def test_tuning_out_of_range_rejected(L, problems):
+    packed = [L.pack_problem(problems[0])]
+    for bad in (dict(rows_per_item=3), dict(words_per_thread=4), dict(table_load_pct=95)):
+        with pytest.raises(L.LsynError) as ei:
+            L.Batch(packed, L.make_config(cache_bytes=64 << 20), L.make_tuning(**bad))
+        assert ei.value.status == L.LSYN_E_INVAL
 
 
 def _plain(L, packed, cfg, max_size):

@@ -71,16 +71,20 @@ def test_scheduler_allocator_returning_null_gives_nomem(L):
         assert not a.live
 
 
-def test_scheduler_job_that_cannot_fit_answers_nomem(L):
-    """A pool of a few MiB cannot hold a problem whose 64 KiB matrices need
-    more than that for their first level: that job answers LSYN_E_NOMEM, the
-    batch itself succeeds and a small problem beside it is answered."""
-    big = W.labelled_problem("big", 3, 32, 2000, 2000, 30, 60, 5, 64, oracle.labeller)
+def test_scheduler_job_that_cannot_fit_is_answered_alone(L):
+    """A 512 MiB pool cannot hold the caches of a problem with 64 KiB matrices
+    and 31 propositions: that job is answered with LSYN_E_NOMEM (its first
+    levels do not fit) or LSYN_E_CACHE_FULL (capped at what the pool gave
+    it), the batch itself succeeds, and a small problem beside it gets the
+    oracle's answer."""
+    big = W.labelled_problem("big", 3, 31, 4096, 4096, 30, 60, 5, 64, L.labeller)
+    packed_big = L.pack_problem(big)
+    assert packed_big.n_traces * 8 == 64 << 10
     small = W.tiny_problem(7, oracle.labeller)
-    tun = L.make_tuning(pool_bytes=4 << 20)
-    with L.Batch([L.pack_problem(big), L.pack_problem(small)], L.make_config(cache_bytes=1 << 30), tun) as b:
+    tun = L.make_tuning(pool_bytes=512 << 20)
+    with L.Batch([packed_big, L.pack_problem(small)], L.make_config(cache_bytes=1 << 30), tun) as b:
         statuses, results, formulas = b.solve(8)
-    assert statuses[0] == L.LSYN_E_NOMEM, statuses
+    assert statuses[0] in (L.LSYN_E_NOMEM, L.LSYN_E_CACHE_FULL) and results[0].found == 0, statuses
     spec = oracle.Spec.from_problem(small)
     assert statuses[1] == L.LSYN_OK and results[1].size == spec.solve(8)[0] and spec.separates(formulas[1])
 

@@ -77,7 +77,7 @@ def _build(tmpdir, name, old, new, occ):
     so = os.path.join(tmpdir, f"{name}.so")
     with open(cpp, "w") as f:
         f.write(mut)
-    subprocess.run(["g++", "-O1", "-std=c++17", "-shared", "-fPIC", "-o", so, cpp], check=True)
+    subprocess.run(["g++", "-O1", "-std=c++17", "-pthread", "-shared", "-fPIC", "-o", so, cpp], check=True)
     return so
 
 
