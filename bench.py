@@ -25,6 +25,7 @@ import subprocess
 import sys
 import threading
 import time
+import types
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
@@ -37,7 +38,8 @@ CACHE_BYTES = 64 << 30
 MAX_SIZE = 16
 LARGE_CACHE_BYTES = 150 * 10**9
 LARGE_WORKLOAD = ("large plain solve: 10 props, 1024+1024 traces, len U[16,64], Bernoulli(p) with p U[0.2,0.8] per "
-                  "prop, hidden size 15, 2048 x uint64 words (16 KiB) per CM, 150 GB cache (cache-full path)")
+                  "prop, hidden size 15, 2048 x uint64 words (16 KiB) per CM, 150 GB cache; every level built "
+                  "completely until the cache fills (the cache-full path; seed 0 separates at size 5 already)")
 E3_WORKLOAD = ("the paper's worked example: 7 positive + 7 negative traces of length 6 over {a, b}, the paper's "
                "grammar (atoms, not, and, X, F, U), minimal size 16, 16 GiB cache")
 
@@ -195,7 +197,7 @@ def _one_problem_workloads():
                     kernels={"unary": "k_unary_c (not/X/F/G level kernel, 512-byte CMs)",
                              "binary": "k_binary_c + k_binary_small_c (and/or/U level kernels, 512-byte CMs)"}),
         "large": dict(make=lambda W, lab, seed: W.large_problem(seed, lab), cache=LARGE_CACHE_BYTES, max_size=15,
-                      op_mask=0x7F, dtype="u64", desc=LARGE_WORKLOAD, steps=3, cpu_levels=(4, 5),
+                      op_mask=0x7F, dtype="u64", desc=LARGE_WORKLOAD, steps=3, cpu_levels=(4, 5), fill=True,
                       kernels={"unary": "k_unary_d (not/X/F/G level kernel, 16 KiB CMs)",
                                "binary": "k_binary_d (and/or/U level kernel, 16 KiB CMs)"}),
         "e3": dict(make=lambda W, lab, seed: _paper_example(W), cache=16 << 30, max_size=16,
@@ -240,13 +242,30 @@ def run_lsyn(args):
     packed = L.pack_problem(problem)
     stream = torch.cuda.current_stream(dev)
     cache = wl["cache"]
-    cfg = L.torch_config(op_mask=wl["op_mask"], cache_bytes=cache, timing=True, stream=stream, device=local)
+    fill = wl.get("fill", False)
+    cfg = L.torch_config(op_mask=wl["op_mask"], cache_bytes=cache, timing=True, stream=stream, device=local,
+                         full_levels=fill)
     ctx = L.lsyn_create(packed, cfg)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
 
+    def run_on(c):
+        if not fill:
+            return L.lsyn_solve(c, wl["max_size"])
+        # every level completely, until the cache is full (or max_size)
+        levels = []
+        for k in range(1, wl["max_size"] + 1):
+            levels.append(L.lsyn_enumerate_level(c, k))
+            if levels[-1].cache_full:
+                break
+        solved = [lv.level for lv in levels if lv.solved]
+        res = types.SimpleNamespace(unique=levels[-1].total, launches=sum(lv.launches for lv in levels),
+                                    constructed=sum(lv.candidates for lv in levels),
+                                    size=solved[0] if solved else 0)
+        return (L.LSYN_E_CACHE_FULL if levels[-1].cache_full else L.LSYN_NOT_FOUND), res, None, levels
+
     def step():
         L.lsyn_reset(ctx)
-        return L.lsyn_solve(ctx, wl["max_size"])
+        return run_on(ctx)
 
     for _ in range(max(args.warmup, 0)):
         st, res, formula, levels = step()
@@ -291,6 +310,8 @@ def run_lsyn(args):
     total_uniques = _reduce_sum(float(uniques), world, dev)
     value = total_uniques / (max_ms / 1000.0)
 
+    L.lsyn_destroy(ctx)  # its memory goes back to the allocator for the end-to-end contexts
+    ctx = None
     # End to end through the public API from pinned host buffers: create
     # (host->device copy of the traces), solve, read the formula back, destroy;
     # L2 flushed before each step as for the device-timed steps.
@@ -306,8 +327,8 @@ def run_lsyn(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         c2 = L.lsyn_create(host_problem, L.torch_config(op_mask=wl["op_mask"], cache_bytes=cache, stream=stream,
-                                                        device=local))
-        st2, r2, f2, _ = L.lsyn_solve(c2, wl["max_size"])
+                                                        device=local, full_levels=fill))
+        st2, r2, f2, _ = run_on(c2)
         L.lsyn_destroy(c2)
         dt = (time.perf_counter() - t0) * 1000.0
         if i > 0:  # the first call warms the allocator cache
@@ -385,7 +406,6 @@ def run_lsyn(args):
                 "hardware": "not named in the paper", "note": "context only: the paper builds every ordered pair "
                 "and names no GPU; this library builds and/or once per unordered pair"}
         print(json.dumps(line), flush=True)
-    L.lsyn_destroy(ctx)
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0

@@ -172,7 +172,12 @@ lsyn_status lsyn_batch_autotune(lsyn_batch* b, int32_t max_size, lsyn_batch_tuni
     res[i].formula = fbuf[i].data();
     res[i].formula_cap = fbuf[i].size();
   }
-  const lsyn_batch_tuning saved = b->eng.tune();
+  // the defaults written out, so that the result names every value it chose
+  lsyn_batch_tuning saved = b->eng.tune();
+  if (!saved.rows_per_item) saved.rows_per_item = 8;
+  if (!saved.words_per_thread) saved.words_per_thread = 1;
+  if (!saved.table_load_pct)
+    saved.table_load_pct = std::max(25, std::min(90, int32_t(b->jobs.empty() ? 50 : b->jobs[0]->c->table_load * 100.0 + 0.5)));
   auto time_it = [&](const lsyn_batch_tuning& t, double* ms) {
     b->eng.set_tune(t);
     const double t0 = now_ms();

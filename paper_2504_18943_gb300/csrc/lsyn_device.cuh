@@ -423,10 +423,14 @@ struct PathA {
         st_release(slot, tag | (unsigned long long)(id + 1u));  // orders this thread's CM and provenance first
         return 1;
       }
+      // A tombstone is left only by a claim past a full arena, and such a
+      // level is incomplete: the candidate could not be inserted any more,
+      // so probing stops (a small table full of tombstones would otherwise
+      // leave it nowhere to stop).
+      if (uint32_t(sv) == kSlotTomb) return 0;
       if ((sv & 0xFFFFFFFF00000000ull) != tag) continue;
       const uint32_t low = uint32_t(sv);
       if (low == kSlotPending) { defer(cv, desc); return 0; }
-      if (low == kSlotTomb) continue;
       const uint4* src = row_ptr(cv, low - 1u);
       uint32_t ne = 0;
 #pragma unroll
@@ -782,7 +786,8 @@ struct PathC {
           state = kClaimed;
         } else {
           const uint32_t low = uint32_t(sv);
-          if ((sv & 0xFFFFFFFF00000000ull) != tag || low == kSlotTomb) pos = (pos + 1) & cv.table_mask;
+          if (low == kSlotTomb) state = kDone;  // the arena is full: this level is incomplete (see path A)
+          else if ((sv & 0xFFFFFFFF00000000ull) != tag) pos = (pos + 1) & cv.table_mask;
           else if (low == kSlotPending) state = kDeferred;
           else {
             need = true;
@@ -1246,7 +1251,8 @@ struct PathD {
           state = kClaimed;
         } else {
           const uint32_t low = uint32_t(sv);
-          if ((sv & 0xFFFFFFFF00000000ull) != tag || low == kSlotTomb) pos = (pos + 1) & cv.table_mask;
+          if (low == kSlotTomb) state = kDone;  // the arena is full: this level is incomplete (see path A)
+          else if ((sv & 0xFFFFFFFF00000000ull) != tag) pos = (pos + 1) & cv.table_mask;
           else if (low == kSlotPending) state = kDeferred;
           else {
             need = true;

@@ -377,31 +377,57 @@ def test_matrices_above_64k_unsupported(L):
 
 
 def test_large_workload_full_size(L):
-    """The large configuration (10 propositions, 1024 + 1024 traces of length
-    16..64, 16 KiB CMs): levels 1..3 equal the oracle's; deeper entries are
-    sampled and re-evaluated one by one by the oracle; the run either solves
-    (minimal: every level below complete) or fills the cache."""
+    """The large configuration at its stated size (10 propositions, 1024 +
+    1024 traces of length 16..64, 16 KiB CMs, a 150 GB cache), levels built
+    completely until the cache fills (the cache-full path): levels 1..5 equal
+    the oracle's as sets (the oracle's levels built on every host core), the
+    first level holding a separating CM is the oracle's minimal size, the
+    last level is marked full and no level holds a duplicate; sampled deep
+    entries re-evaluate, one by one, to their CM."""
+    import os
+    import torch
     p = W.large_problem(0, oracle.labeller)
     assert p.n_traces == 2048 and p.word_bits == 64
     spec = oracle.Spec.from_problem(p)
-    assert_levels_match(L, p, 3, cache_bytes=2 << 30, spec=spec)
+    depth = 5
+    run = spec.enumerate_threads(depth, max(1, len(os.sched_getaffinity(0))))
+    words = {k: oracle_level_words(run, k, p.traces.lengths, 64) for k in range(1, depth + 1)}
+    del run
+    pos = np.arange(p.n_traces) < p.n_pos
+
+    def separating(w):  # position 0 (bit 0) set on every positive trace, clear on every negative one
+        b0 = (w & np.uint64(1)).astype(bool)
+        return np.all(b0 == pos[None, :], axis=1)
+
+    oracle_min = next((k for k in range(1, depth + 1) if separating(words[k]).any()), None)
+    want = {k: sorted_rows(w) for k, w in words.items()}
+    del words
+    torch.cuda.empty_cache()
     packed = L.pack_problem(p)
-    with L.Synthesizer(packed, L.torch_config(cache_bytes=24 << 30)) as s:
-        st, res, f, levels = s.solve(15)
-        assert st in (L.LSYN_OK, L.LSYN_E_CACHE_FULL), L.lsyn_last_error(s.ctx)
-        if st == L.LSYN_OK:
-            assert spec.separates(f) and W.formula_size(f) == res.size
-        else:
-            assert levels[-1].cache_full == 1 and res.found == 0
+    with L.Synthesizer(packed, L.torch_config(cache_bytes=150 * 10**9, full_levels=True)) as s:
+        levels = []
+        for k in range(1, 16):
+            levels.append(s.level(k))
+            if levels[-1].cache_full:
+                break
+        assert levels[-1].cache_full == 1, "150 GB did not fill by level 15"
+        assert len(levels) > depth
+        gpu_min = next((lv.level for lv in levels if lv.solved), None)
+        assert gpu_min == oracle_min, (gpu_min, oracle_min)
+        for k in range(1, depth + 1):
+            got = sorted_rows(s.export(k))
+            assert np.array_equal(got, want[k]), f"level {k} differs from the oracle"
         rng = np.random.default_rng(0)
-        for k in range(1, res.levels_done + 1):
+        for k in range(depth + 1, len(levels) + 1):
             n = s.count(k)
-            rows = s.export(k, 0, min(n, 4000))
-            assert canon(rows).shape[0] == rows.shape[0], f"duplicates in level {k}"
+            rows = s.export(k, 0, min(n, 20000))
+            assert not has_duplicates(sorted_rows(rows)), f"duplicates in level {k}"
             for idx in rng.choice(n, size=min(n, 4), replace=False):
                 f_k = s.formula(k, int(idx))
                 cm = oracle_rows([spec.eval(f_k)], 64, p.n_traces)[0]
                 assert np.array_equal(cm, s.export(k, int(idx), 1)[0]) and W.formula_size(f_k) == k
+    print(f"large workload: minimal size {gpu_min}, cache full at level {len(levels)}, "
+          f"level sizes {[lv.unique for lv in levels]}")
 
 
 @pytest.mark.parametrize("word_bits,n_traces", [(32, 40), (32, 100), (64, 44), (32, 140), (64, 90), (64, 130)])
