@@ -311,16 +311,33 @@ __device__ __forceinline__ void st_release(unsigned long long* p, unsigned long 
   asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// One probe of a table slot: claims it if empty (0), else returns what is
-// there. Acquire semantics: when the value is a published id, the writer's
-// release (fence.acq_rel.gpu, then a relaxed store of the slot) synchronises
-// with this read, so the entry's CM row, stored before the release, is visible
-// to this thread's later reads, and, after a warp barrier, to its warp's.
 __device__ __forceinline__ unsigned long long cas_acquire(unsigned long long* p, unsigned long long cmp,
                                                           unsigned long long val) {
   unsigned long long old;
   asm volatile("atom.acquire.gpu.global.cas.b64 %0, [%1], %2, %3;" : "=l"(old) : "l"(p), "l"(cmp), "l"(val) : "memory");
   return old;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// One probe of a table slot: returns what is there, after claiming the slot
+// with `val` if it was empty (then 0). The slot is read first and claimed with
+// a compare-and-swap only when it reads empty: most probes meet an occupied
+// slot (an equal CM, or another tag), and on this GPU a random load costs far
+// less than a random atomic (whole solves 1.45x faster than one CAS per probe).
+// A claim that loses a race returns the winner's value, as the CAS alone
+// would. Acquire semantics (load and CAS): when the value is a published id,
+// the writer's release (fence.acq_rel.gpu, then a relaxed store of the slot)
+// synchronises with this read, so the entry's CM row, stored before the
+// release, is visible to this thread's later reads, and, after a warp
+// barrier, to its warp's.
+__device__ __forceinline__ unsigned long long probe_slot(unsigned long long* p, unsigned long long val) {
+  const unsigned long long sv = ld_acquire_u64(p);
+  return sv != 0ull ? sv : cas_acquire(p, 0ull, val);
 }
 
 __device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
@@ -405,8 +422,8 @@ struct PathA {
     unsigned long long pos = h & cv.table_mask;
     for (unsigned long long it = 0; it <= cv.table_mask; ++it, pos = (pos + 1) & cv.table_mask) {
       unsigned long long* slot = cv.table + pos;
-      // One atomic per probe: claims an empty slot, or returns what is there.
-      const unsigned long long sv = cas_acquire(slot, 0ull, tag | kSlotPending);
+      // Claims an empty slot, or returns what is there.
+      const unsigned long long sv = probe_slot(slot, tag | kSlotPending);
       if (sv == 0ull) {
         const unsigned id = atomicAdd(&cv.ctr->n_entries, 1u);
         if (id >= cv.max_entries) {
@@ -780,8 +797,8 @@ struct PathC {
     while (true) {
       bool need = false;
       if (state == kProbing) {
-        // One atomic per probe: claims an empty slot, or returns what is there.
-        const unsigned long long sv = cas_acquire(cv.table + pos, 0ull, tag | kSlotPending);
+        // Claims an empty slot, or returns what is there.
+        const unsigned long long sv = probe_slot(cv.table + pos, tag | kSlotPending);
         if (sv == 0ull) {
           state = kClaimed;
         } else {
@@ -1246,7 +1263,7 @@ struct PathD {
     while (true) {
       bool need = false;
       if (state == kProbing) {
-        const unsigned long long sv = cas_acquire(cv.table + pos, 0ull, tag | kSlotPending);
+        const unsigned long long sv = probe_slot(cv.table + pos, tag | kSlotPending);
         if (sv == 0ull) {
           state = kClaimed;
         } else {
