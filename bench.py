@@ -201,7 +201,7 @@ def _one_problem_workloads():
                       kernels={"unary": "k_unary_d (not/X/F/G level kernel, 16 KiB CMs)",
                                "binary": "k_binary_d (and/or/U level kernel, 16 KiB CMs)"}),
         "e3": dict(make=lambda W, lab, seed: _paper_example(W), cache=16 << 30, max_size=16,
-                   op_mask=0x1B | 0x40, dtype="u32", desc=E3_WORKLOAD, steps=5, cpu_levels=(7, 8),
+                   op_mask=0x1B | 0x40, dtype="u32", desc=E3_WORKLOAD, steps=5, cpu_levels=(12, 14),
                    kernels={"unary": "k_unary_a (not/X/F/G level kernel, 64-byte CMs)",
                             "binary": "k_binary_a (and/U level kernel, 64-byte CMs)"}),
     }

@@ -367,11 +367,21 @@ __device__ __forceinline__ const uint4* row_ptr(const CacheView& cv, uint32_t id
   return cv.arena + size_t(id) * cv.vecs;
 }
 
-// Pair `local` of a split, as row offsets (left, right): row-major over
-// left x right, or, for a level paired with itself, the pairs a < b in order
-// of b (b = 1, 2, ...; a = 0 .. b-1), so that no pair index is wasted.
-__device__ __forceinline__ uint2 split_pair(const Split& S, unsigned long long local) {
+// Pair `local` of a split, as row offsets (left, right). For a level paired
+// with itself: the pairs a < b in order of b (b = 1, 2, ...; a = 0 .. b-1), so
+// that no pair index is wasted. Otherwise, with large_outer, the right
+// (larger) side's rows in order, each with every row of the left (smaller)
+// side: each large row is read once while the small side stays in L2, which
+// made 16 KiB CMs (path D) 15 % faster at the large workload's level 8 than
+// the left-major order; without it, row-major over left x right, which
+// measured faster for CMs of up to 128 bytes (path A), whose levels L2 holds
+// anyway.
+__device__ __forceinline__ uint2 split_pair(const Split& S, unsigned long long local, bool large_outer) {
   if (!S.tri) {
+    if (large_outer) {
+      const uint32_t ib = uint32_t(local / S.left_n);
+      return make_uint2(uint32_t(local - (unsigned long long)ib * S.left_n), ib);
+    }
     const uint32_t ia = uint32_t(local / S.right_n);
     return make_uint2(ia, uint32_t(local - (unsigned long long)ia * S.right_n));
   }
@@ -507,7 +517,7 @@ __global__ void __launch_bounds__(256) k_binary_a(CacheView cv, BinaryPlan plan)
     int sp = 0;
     while (sp + 1 < plan.n_splits && plan.s[sp + 1].pairs_begin <= p) ++sp;
     const Split& S = plan.s[sp];
-    const uint2 ab = split_pair(S, p - S.pairs_begin);
+    const uint2 ab = split_pair(S, p - S.pairs_begin, false);
     const uint32_t a_id = S.left_start + ab.x, b_id = S.right_start + ab.y;
     const bool full = ld_relaxed_u32(&cv.ctr->full) != 0u;
     uint4 a[V], b[V];
@@ -1219,18 +1229,36 @@ struct PathD {
     const int lane = threadIdx.x & 31;
     const unsigned rv = cv.vecs >> 5;
     uint32_t my_lo = 0, my_hi = 0, bad = 0;
-    for (int q = 0; q < n; ++q) {
-      uint64_t acc = 0;
-      uint32_t diff = 0;
-      each_vec(gen, q, rv, [&](unsigned v, const uint4& c) {
-        acc = h_mac(c, __ldg(cv.hmul + v), acc);
-        if (v < cv.plane_vecs) diff |= bit0s<W>(c) ^ bit0s<W>(__ldg(cv.label + v));  // position 0: plane 0
-      });
-      const uint32_t lo = __reduce_add_sync(kFull, uint32_t(acc));
-      const uint32_t hi = __reduce_add_sync(kFull, uint32_t(acc >> 32));
-      my_lo = lane == q ? lo : my_lo;
-      my_hi = lane == q ? hi : my_hi;
-      bad |= (diff != 0u ? 1u : 0u) << q;
+    // Four candidates at a time (one operand group and its four operators, or
+    // four descriptors): one pass over this lane's vectors, VPT at a time.
+    for (int q0 = 0; q0 < n; q0 += 4) {
+      uint64_t acc[4] = {0, 0, 0, 0};
+      uint32_t diff[4] = {0, 0, 0, 0};
+      for (unsigned r = 0; r < rv; r += VPT) {
+#pragma unroll
+        for (int u = 0; u < VPT; ++u) {
+          if (r + u >= rv) break;
+          const unsigned v = lane + 32u * (r + u);
+          uint4 c[4];
+          gen.compute4(q0, v, c);
+          const uint4 mul = __ldg(cv.hmul + v);
+          const uint32_t lab = v < cv.plane_vecs ? bit0s<W>(__ldg(cv.label + v)) : 0u;
+#pragma unroll
+          for (int o = 0; o < 4; ++o) {
+            acc[o] = h_mac(c[o], mul, acc[o]);
+            if (v < cv.plane_vecs) diff[o] |= bit0s<W>(c[o]) ^ lab;  // position 0: plane 0
+          }
+        }
+      }
+#pragma unroll
+      for (int o = 0; o < 4; ++o) {
+        const int q = q0 + o;
+        const uint32_t lo = __reduce_add_sync(kFull, uint32_t(acc[o]));
+        const uint32_t hi = __reduce_add_sync(kFull, uint32_t(acc[o] >> 32));
+        my_lo = lane == q ? lo : my_lo;
+        my_hi = lane == q ? hi : my_hi;
+        if (q < 32) bad |= (diff[o] != 0u ? 1u : 0u) << q;
+      }
     }
     bad = __reduce_or_sync(kFull, bad);
     const bool mine = lane < n && ((en >> lane) & 1u);
@@ -1355,6 +1383,25 @@ struct PairGenD {
       default: return row_op<W>(*cv, kUntil, b, a, v);
     }
   }
+  // vector v of candidates q0 .. q0 + 3 (one pair, its four operators): the
+  // operands' vectors are read once
+  __device__ void compute4(int q0, unsigned v, uint4 (&c)[4]) const {
+    const uint2 pr = pairs[q0 >> 2];
+    const uint4* a = row_ptr(*cv, pr.x);
+    const uint4* b = row_ptr(*cv, pr.y);
+    if (cv->planes > 1) {
+      c[0] = row_op<W>(*cv, kAnd, a, b, v);
+      c[1] = row_op<W>(*cv, kOr, a, b, v);
+      c[2] = row_op<W>(*cv, kUntil, a, b, v);
+      c[3] = row_op<W>(*cv, kUntil, b, a, v);
+      return;
+    }
+    const uint4 x = __ldg(a + v), y = __ldg(b + v);
+    c[0] = v_op<W>(kAnd, x, y, y, 0);
+    c[1] = v_op<W>(kOr, x, y, y, 0);
+    c[2] = v_op<W>(kUntil, x, y, y, 0);
+    c[3] = v_op<W>(kUntil, y, x, y, 0);
+  }
   __device__ uint64_t desc(int q) const {
     const uint2 pr = pairs[q >> 2];
     switch (q & 3) {
@@ -1374,6 +1421,18 @@ struct RowGenD {
     const uint4* a = row_ptr(*cv, id0 + uint32_t(q >> 2));
     return row_op<W>(*cv, unary_code(q & 3), a, a, v);
   }
+  // vector v of candidates q0 .. q0 + 3 (one row, its four operators)
+  __device__ void compute4(int q0, unsigned v, uint4 (&c)[4]) const {
+    const uint4* a = row_ptr(*cv, id0 + uint32_t(q0 >> 2));
+    if (cv->planes > 1) {
+#pragma unroll
+      for (int o = 0; o < 4; ++o) c[o] = row_op<W>(*cv, unary_code(o), a, a, v);
+      return;
+    }
+    const uint4 x = __ldg(a + v), lm = __ldg(cv->lenmask + v);
+#pragma unroll
+    for (int o = 0; o < 4; ++o) c[o] = v_op<W>(unary_code(o), x, x, lm, 0);
+  }
   __device__ uint64_t desc(int q) const { return pack_desc(unary_code(q & 3), id0 + uint32_t(q >> 2), 0); }
 };
 
@@ -1388,6 +1447,11 @@ struct ListGenD {
     const uint4* a = row_ptr(*cv, desc_left(dd));
     const uint4* b = (op == kAnd || op == kOr || op == kUntil) ? row_ptr(*cv, desc_right(dd)) : a;
     return row_op<W>(*cv, op, a, b, v);
+  }
+  // four independent descriptors (the batch is padded with harmless atoms)
+  __device__ void compute4(int q0, unsigned v, uint4 (&c)[4]) const {
+#pragma unroll
+    for (int o = 0; o < 4; ++o) c[o] = compute(q0 + o, v);
   }
   __device__ uint64_t desc(int q) const { return d[q]; }
 };
@@ -1446,7 +1510,7 @@ __global__ void __launch_bounds__(256) k_binary_d(CacheView cv, BinaryPlan plan)
         int sp = 0;
         while (sp + 1 < plan.n_splits && plan.s[sp + 1].pairs_begin <= pidx) ++sp;
         const Split& S = plan.s[sp];
-        const uint2 ab = split_pair(S, pidx - S.pairs_begin);
+        const uint2 ab = split_pair(S, pidx - S.pairs_begin, true);
         pr = make_uint2(S.left_start + ab.x, S.right_start + ab.y);
       }
       s_pairs[wib][lane] = pr;
@@ -1673,7 +1737,7 @@ __global__ void __launch_bounds__(256) k_batch_run(StepHeader* hdr, const StepPr
       bool valid = pidx < end;
       uint2 pr = make_uint2(0, 0);
       if (valid) {
-        const uint2 ab = split_pair(S, pidx - S.pairs_begin);
+        const uint2 ab = split_pair(S, pidx - S.pairs_begin, cv->vecs > 8u);  // path D jobs: large side outer
         pr = make_uint2(S.left_start + ab.x, S.right_start + ab.y);
       }
       s_pairs[wib][lane] = pr;
