@@ -592,6 +592,8 @@ def run_served(args):
             # every repeat draws its own arrival times (seed = repeat)
             arrivals = W.poisson_arrivals(rep, rate, args.duration)
             order = [i % BATCH_N for i in range(len(arrivals))]
+            torch.cuda.synchronize()
+            torch.cuda.empty_cache()  # the server's pool takes its share of what is free now
             with L.Server(cfg) as sv:
                 for q in packed[:8]:  # warm the pool and the launch paths
                     sv.wait(sv.submit(q, BATCH_MAX_SIZE))
@@ -622,7 +624,9 @@ def run_served(args):
                                       "p50_ms": _percentile(plat, 0.5), "p99_ms": _percentile(plat, 0.99)},
                    "sched": {k: stats[k] for k in ("steps", "large_levels", "evictions", "redos", "pool_peak")}}
             if args.plain_live:
+                torch.cuda.synchronize()
                 plive, answers, t_last = _plain_fifo_live(L, packed, arrivals, order, BATCH_MAX_SIZE, BATCH_CACHE)
+                torch.cuda.empty_cache()
                 run["plain_live"] = {"problems_per_s": len(arrivals) / t_last, "p50_ms": _percentile(plive, 0.5),
                                      "p99_ms": _percentile(plive, 0.99),
                                      "answers_differ": sum(1 for a, (st, r, f) in zip(answers, res)
