@@ -1307,17 +1307,32 @@ struct PathD {
       }
       const uint32_t need_m = __ballot_sync(kFull, need);
       if (need_m) __syncwarp();  // the probing lanes' acquires, before every lane's row reads
-      for (uint32_t m = need_m; m; m &= m - 1u) {
-        const int q = __ffs(m) - 1;
-        const uint32_t id = __shfl_sync(kFull, cmp_id, q);
-        const uint4* src = row_ptr(cv, id);  // published: visible in L2, read past L1
-        uint32_t ne = 0;
-        each_vec(gen, q, rv, [&](unsigned v, const uint4& c) { ne |= v_ne(__ldcg(src + v), c); });
-        const bool eq = !__any_sync(kFull, ne != 0u);
-        if (lane == q) {
-          if (eq) state = kDone;
-          else pos = (pos + 1) & cv.table_mask;
+      // The tag matches of one operand group (four candidates) are compared in
+      // one pass over its vectors, so the operands are read once per group.
+      uint32_t ne_m = 0;  // bit q: candidate q differs from the row its probe found
+      for (uint32_t gm = need_m; gm;) {
+        const int g = (__ffs(gm) - 1) >> 2;
+        const uint32_t sub = (need_m >> (4 * g)) & 0xFu;  // warp-uniform
+        gm &= ~(0xFu << (4 * g));
+        const uint4* src[4];
+#pragma unroll
+        for (int o = 0; o < 4; ++o) src[o] = row_ptr(cv, __shfl_sync(kFull, cmp_id, 4 * g + o));  // published rows, read past L1
+        uint32_t ne[4] = {0u, 0u, 0u, 0u};
+        for (unsigned r = 0; r < rv; ++r) {
+          const unsigned v = lane + 32u * r;
+          uint4 c[4];
+          gen.compute4(4 * g, v, c, sub);
+#pragma unroll
+          for (int o = 0; o < 4; ++o)
+            if ((sub >> o) & 1u) ne[o] |= v_ne(__ldcg(src[o] + v), c[o]);
         }
+#pragma unroll
+        for (int o = 0; o < 4; ++o)
+          if (((sub >> o) & 1u) && __any_sync(kFull, ne[o] != 0u)) ne_m |= 1u << (4 * g + o);
+      }
+      if ((need_m >> lane) & 1u) {
+        if (!((ne_m >> lane) & 1u)) state = kDone;  // equal CM already cached
+        else pos = (pos + 1) & cv.table_mask;
       }
       if (!__any_sync(kFull, state == kProbing)) break;
       if (++guard > cv.table_mask) {
@@ -1335,13 +1350,26 @@ struct PathD {
     if (!kEarlyPublish) WarpDedup::flush(pend);
     if (claim) {
       const unsigned fresh = WarpDedup::take(ids, n_claim, have, base, use_pre);
-      unsigned rank = 0;
-      for (uint32_t m = claim; m; m &= m - 1u, ++rank) {
-        const int q = __ffs(m) - 1;
-        const unsigned id = rank < have ? ids.next + rank : fresh + (rank - have);
-        if (id < cv.max_entries) {
-          uint4* dst = cv.arena + size_t(id) * cv.vecs;
-          each_vec(gen, q, rv, [&](unsigned v, const uint4& c) { dst[v] = c; });
+      // the rows of one operand group's claims in one pass over its vectors
+      for (uint32_t gm = claim; gm;) {
+        const int g = (__ffs(gm) - 1) >> 2;
+        const uint32_t sub = (claim >> (4 * g)) & 0xFu;  // warp-uniform
+        gm &= ~(0xFu << (4 * g));
+        uint4* dst[4];
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+          const int q = 4 * g + o;
+          const unsigned rank = unsigned(__popc(claim & ((1u << q) - 1u)));  // ids go by rank among the claims
+          const unsigned id = rank < have ? ids.next + rank : fresh + (rank - have);
+          dst[o] = ((sub >> o) & 1u) && id < cv.max_entries ? cv.arena + size_t(id) * cv.vecs : nullptr;
+        }
+        for (unsigned r = 0; r < rv; ++r) {
+          const unsigned v = lane + 32u * r;
+          uint4 c[4];
+          gen.compute4(4 * g, v, c, sub);
+#pragma unroll
+          for (int o = 0; o < 4; ++o)
+            if (dst[o]) dst[o][v] = c[o];
         }
       }
       const unsigned my_rank = unsigned(__popc(claim & ((1u << lane) - 1u)));
@@ -1384,8 +1412,8 @@ struct PairGenD {
     }
   }
   // vector v of candidates q0 .. q0 + 3 (one pair, its four operators): the
-  // operands' vectors are read once
-  __device__ void compute4(int q0, unsigned v, uint4 (&c)[4]) const {
+  // operands' vectors are read once (all four are computed whatever `sub` asks)
+  __device__ void compute4(int q0, unsigned v, uint4 (&c)[4], uint32_t /*sub*/ = 0xFu) const {
     const uint2 pr = pairs[q0 >> 2];
     const uint4* a = row_ptr(*cv, pr.x);
     const uint4* b = row_ptr(*cv, pr.y);
@@ -1422,7 +1450,7 @@ struct RowGenD {
     return row_op<W>(*cv, unary_code(q & 3), a, a, v);
   }
   // vector v of candidates q0 .. q0 + 3 (one row, its four operators)
-  __device__ void compute4(int q0, unsigned v, uint4 (&c)[4]) const {
+  __device__ void compute4(int q0, unsigned v, uint4 (&c)[4], uint32_t /*sub*/ = 0xFu) const {
     const uint4* a = row_ptr(*cv, id0 + uint32_t(q0 >> 2));
     if (cv->planes > 1) {
 #pragma unroll
@@ -1448,10 +1476,11 @@ struct ListGenD {
     const uint4* b = (op == kAnd || op == kOr || op == kUntil) ? row_ptr(*cv, desc_right(dd)) : a;
     return row_op<W>(*cv, op, a, b, v);
   }
-  // four independent descriptors (the batch is padded with harmless atoms)
-  __device__ void compute4(int q0, unsigned v, uint4 (&c)[4]) const {
+  // four independent descriptors (the batch is padded with harmless atoms):
+  // only those in `sub` are computed
+  __device__ void compute4(int q0, unsigned v, uint4 (&c)[4], uint32_t sub = 0xFu) const {
 #pragma unroll
-    for (int o = 0; o < 4; ++o) c[o] = compute(q0 + o, v);
+    for (int o = 0; o < 4; ++o) c[o] = ((sub >> o) & 1u) ? compute(q0 + o, v) : make_uint4(0, 0, 0, 0);
   }
   __device__ uint64_t desc(int q) const { return d[q]; }
 };
