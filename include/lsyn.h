@@ -55,7 +55,7 @@ typedef enum {
   LSYN_E_INVAL = -1,        /* an argument is out of range or inconsistent */
   LSYN_E_NOMEM = -2,        /* a device allocation failed */
   LSYN_E_CUDA = -3,         /* a CUDA runtime call failed */
-  LSYN_E_UNSUPPORTED = -4,  /* a valid request this build does not handle */
+  LSYN_E_UNSUPPORTED = -4,  /* a valid request the library does not handle (CMs above 64 KiB) */
   LSYN_E_CACHE_FULL = -5,   /* the language cache ran out of space: deeper levels cannot be built */
   LSYN_E_TIMEOUT = -6,      /* a deadline passed between levels */
   LSYN_E_STATE = -7         /* call out of order, or an internal consistency check failed */

@@ -570,7 +570,7 @@ lsyn_status lsyn::ctx_shell(const lsyn_problem* problem, const lsyn_config* conf
     vecs = plane_vecs * unsigned(L.planes);
   } else {
     g_create_error = "characteristic matrices above 64 KiB (" + std::to_string(L.vecs_needed * 16) +
-                     " bytes) are not supported by this build";
+                     " bytes) are not supported: at most 64 KiB";
     return LSYN_E_UNSUPPORTED;
   }
   const size_t M = size_t(vecs) * 16;
