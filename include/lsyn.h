@@ -138,8 +138,14 @@ typedef void (*lsyn_free_fn)(void* ptr, void* user);
  *                level after the first one it builds, whether this much time
  *                has passed since it was called, and if so stops with
  *                LSYN_E_TIMEOUT; the levels built so far stay complete and a
- *                later lsyn_solve continues from them. A level that has
- *                started is not interrupted.
+ *                later lsyn_solve continues from them. A later level (not the
+ *                first the call builds, which always runs to its end) that is
+ *                running when the limit passes is stopped by its kernels at their next
+ *                poll (every few warp batches; once per tile), and lsyn_solve
+ *                returns LSYN_E_TIMEOUT with out->levels_done complete levels;
+ *                the interrupted level's entries are in the cache, so the
+ *                context answers LSYN_E_STATE until it is reset (lsyn_reset).
+ *                lsyn_enumerate_level on its own keeps no time limit.
  * The fields after `device` were added later; a zero-filled struct keeps every
  * default.
  */

@@ -44,6 +44,10 @@ double lsyn::now_ms() {
 namespace {
 
 __global__ void k_level_begin(DevCounters* c) {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  c->t0 = t;
+  c->timed_out = 0;
   c->full = 0;
   c->solved = 0;
   c->error = 0;
@@ -693,6 +697,7 @@ lsyn_status lsyn_reset(lsyn_ctx* c) {
   c->level_n.assign(1, 0);
   c->levels_done = 0;
   c->last_incomplete = false;
+  c->needs_reset = false;
   c->constructed = 0;
   c->last_sol = ~0ull;
   return LSYN_OK;
@@ -701,6 +706,7 @@ lsyn_status lsyn_reset(lsyn_ctx* c) {
 lsyn_status lsyn_enumerate_level(lsyn_ctx* c, int32_t k, lsyn_level_stats* out) {
   if (!c) return LSYN_E_INVAL;
   if (c->borrowed) return c->fail(LSYN_E_STATE, "a batch or server problem is driven by its owner");
+  if (c->needs_reset) return c->fail(LSYN_E_STATE, "a level was interrupted by the time limit: reset the context");
   if (k != c->levels_done + 1) return c->fail(LSYN_E_STATE, "level k must be levels_done + 1");
   if (c->last_incomplete) return c->fail(LSYN_E_STATE, "the previous level is incomplete (cache full or stopped early)");
   if (k > 64) return c->fail(LSYN_E_INVAL, "levels above 64 are not supported");
@@ -724,6 +730,12 @@ lsyn_status lsyn_enumerate_level(lsyn_ctx* c, int32_t k, lsyn_level_stats* out) 
   ctx_level_plan(c, k, &lp);
   const uint32_t start = lp.start;
   int launches = 0;
+  // inside lsyn_solve with a time limit: what is left of it is this level's budget
+  c->level_budget_ns = 0;
+  if (c->solve_deadline_ms > 0) {
+    const double left_ms = c->solve_deadline_ms - t0;
+    c->level_budget_ns = left_ms > 0 ? (unsigned long long)(left_ms * 1e6) + 1ull : 1ull;
+  }
   ev_begin();
   k_level_begin<<<1, 1, 0, c->stream>>>(c->ctr);
   ++launches;
@@ -799,6 +811,7 @@ lsyn_status lsyn_enumerate_level(lsyn_ctx* c, int32_t k, lsyn_level_stats* out) 
   int cur = 1;
   for (int npass = 1;; ++npass) {
     const DevCounters& h = c->h_snap[snap - 1].c;
+    if (h.timed_out) break;  // reported below
     if (h.defer_overflow) return c->fail(LSYN_E_STATE, "deferred list overflow: the level is not exact");
     if (h.error == 1) return c->fail(LSYN_E_STATE, "hash table probe overflow");
     if (h.error) break;  // reported below
@@ -813,6 +826,11 @@ lsyn_status lsyn_enumerate_level(lsyn_ctx* c, int32_t k, lsyn_level_stats* out) 
     if (std::min(c->h_snap[snap - 1].c.defer_n[cur], c->defer_cap) == 0 && (ls = close_holes()) != LSYN_OK) return ls;
   }
   const DevCounters& h = c->h_snap[snap - 1].c;
+  if (h.timed_out) {
+    c->needs_reset = true;  // the level is partial, and its entries are in the cache
+    return c->fail(LSYN_E_TIMEOUT, "time limit passed during level " + std::to_string(k) +
+                                       ": the level is incomplete; reset the context before using it again");
+  }
   if (h.error) {
     static const char* const what[] = {"", "hash table probe overflow", "hole log overflow",
                                        "hole fixup found an inconsistent slot", "inconsistent hole log"};
@@ -863,6 +881,9 @@ lsyn_status lsyn_solve(lsyn_ctx* c, int32_t max_size, lsyn_result* out) {
   lsyn_status result = LSYN_NOT_FOUND;
   const int first_k = c->levels_done + 1;
   for (int k = first_k; k <= max_size; ++k) {
+    // the first level of the call always runs to its end; the later ones get
+    // what is left of the limit as their budget inside the kernels
+    c->solve_deadline_ms = c->time_limit_ms > 0 && k > first_k ? t0 + c->time_limit_ms : 0;
     // the deadline is checked between levels: the first level of the call always runs
     if (c->time_limit_ms > 0 && k > first_k && now_ms() - t0 >= c->time_limit_ms) {
       c->err = "time limit of " + std::to_string(c->time_limit_ms) + " ms passed before level " + std::to_string(k);
@@ -890,6 +911,8 @@ lsyn_status lsyn_solve(lsyn_ctx* c, int32_t max_size, lsyn_result* out) {
       break;
     }
   }
+  c->solve_deadline_ms = 0;
+  c->level_budget_ns = 0;
   out->levels_done = c->levels_done;
   out->constructed = int64_t(c->constructed);
   out->unique = int64_t(c->level_start.back() + c->level_n.back());

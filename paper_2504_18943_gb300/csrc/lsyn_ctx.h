@@ -108,7 +108,10 @@ struct lsyn_ctx {
   bool owns_host = false;  // h_snap / h_fbuf / h_fstatus are this context's pinned buffers
   double table_load = 0.5;
   unsigned tile_rows = 0;      // forced block-tile rows of the 512-byte binary launch (0: automatic)
-  double time_limit_ms = 0;    // lsyn_solve's deadline between levels (0: none)
+  double time_limit_ms = 0;    // lsyn_solve's time limit (0: none)
+  double solve_deadline_ms = 0;  // host clock (now_ms) at which the running lsyn_solve's limit passes (0: none)
+  unsigned long long level_budget_ns = 0;  // the running level's time budget (CacheView::time_budget_ns)
+  bool needs_reset = false;    // a level was interrupted by the time limit: only lsyn_reset helps
   // problem
   int n_props = 0, n_pos = 0, n_neg = 0, T = 0, word_bits = 32, max_len = 1, steps = 0;
   unsigned vecs = 0;
@@ -186,6 +189,7 @@ struct lsyn_ctx {
     cv.early_exit = full_levels ? 0 : 1;
     cv.planes = planes;
     cv.plane_vecs = plane_vecs;
+    cv.time_budget_ns = level_budget_ns;
     return cv;
   }
 };

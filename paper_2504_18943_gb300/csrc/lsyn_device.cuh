@@ -346,8 +346,21 @@ __device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
   return v;
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Polled by the level kernels every few batches (once per tile): a solution
+// was found (with early exit), or the level's time budget is spent.
 __device__ __forceinline__ bool stop_requested(const CacheView& cv) {
-  return cv.early_exit && ld_relaxed_u32(&cv.ctr->solved) != 0u;
+  if (cv.early_exit && ld_relaxed_u32(&cv.ctr->solved) != 0u) return true;
+  if (cv.time_budget_ns && global_ns() - cv.ctr->t0 > cv.time_budget_ns) {
+    cv.ctr->timed_out = 1u;
+    return true;
+  }
+  return false;
 }
 
 __device__ __forceinline__ void record_solution(const CacheView& cv, uint64_t desc) {
@@ -1815,6 +1828,7 @@ static __global__ void k_batch_begin(StepHeader* hdr, const StepProblem* steps, 
   c->built = 0;
   c->inserted = 0;
   c->sol = ~0ull;
+  c->timed_out = 0;
   for (int i = 0; i < 8; ++i) c->work[i] = 0;  // tile counters of one-problem launches in the step
 }
 

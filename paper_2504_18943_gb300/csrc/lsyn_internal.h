@@ -52,7 +52,9 @@ struct alignas(128) DevCounters {
   unsigned int full;             // an insert found the arena full
   unsigned int solved;           // a separating candidate was found (early exit flag)
   unsigned int error;            // internal consistency codes (probe overflow, hole log)
-  unsigned int pad1[26];
+  unsigned long long t0;         // the GPU's global timer (ns) when the level began
+  unsigned int timed_out;        // a kernel stopped because the level's time budget was spent
+  unsigned int pad1[23];
   // ---- deferred lists and the hole log ----
   unsigned int defer_n[2];       // deferred-list fills (ping-pong)
   unsigned int defer_overflow;   // a deferred list overflowed: exactness lost
@@ -96,6 +98,7 @@ struct CacheView {
   int early_exit;                // 1: stop at the first separating candidate
   unsigned int planes;           // words per trace: plane j holds positions [j w, (j + 1) w) of every trace
   unsigned int plane_vecs;       // vectors of one plane (vecs = planes x plane_vecs, then padding)
+  unsigned long long time_budget_ns;  // 0: none; else stop once the global timer passes ctr->t0 + this
 };
 
 // One split {i, j} of level k (i + j = k - 1) for the binary operators.

@@ -145,3 +145,36 @@ def test_time_limit_stops_between_levels_and_solving_continues(L):
     assert st == L.LSYN_OK and res.size == r0.size and calls == r0.size
     spec = oracle.Spec.from_problem(p)
     assert spec.separates(f) and W.formula_size(f) == res.size
+
+
+def test_time_limit_interrupts_a_running_level_and_reset_recovers(L):
+    """A limit that passes while a level runs stops its kernels at their next
+    poll (every few batches, once per tile): lsyn_solve returns LSYN_E_TIMEOUT
+    with the complete levels counted, the context refuses further levels until
+    it is reset, and after lsyn_reset it solves to the same size."""
+    p = W.mid_problem(2, oracle.labeller)
+    packed = L.pack_problem(p)
+    with L.Synthesizer(packed, L.torch_config(cache_bytes=32 << 30, timing=True)) as ref:
+        ref.solve(16)  # warm
+        ref.reset()
+        st0, r0, f0, levels = ref.solve(16)
+    assert st0 == L.LSYN_OK and r0.size == 11
+    before10 = sum(lv.ms for lv in levels if lv.level < 10)
+    level10 = next(lv.ms for lv in levels if lv.level == 10)
+    assert level10 > 2.0, level10  # a level long enough to be cut in its middle
+    limit = before10 + 0.4 * level10
+    with L.Synthesizer(packed, L.torch_config(cache_bytes=32 << 30, time_limit_ms=limit)) as s:
+        st, res, f, built = s.solve(16)
+        assert st == L.LSYN_E_TIMEOUT, (st, res.levels_done)
+        msg = L.lsyn_last_error(s.ctx)
+        assert "during level" in msg or "before level" in msg, msg
+        if "during level" in msg:
+            assert res.levels_done < 11
+            with pytest.raises(L.LsynError) as ei:
+                s.level(res.levels_done + 1)
+            assert ei.value.status == L.LSYN_E_STATE
+        s.reset()
+        assert [s.level(k).unique for k in (1, 2, 3)] == [lv.unique for lv in levels[:3]]
+    with L.Synthesizer(packed, L.torch_config(cache_bytes=32 << 30)) as s2:
+        st2, r2, f2, _ = s2.solve(16)
+    assert st2 == L.LSYN_OK and r2.size == r0.size
