@@ -55,8 +55,7 @@ __global__ void k_level_begin(DevCounters* c) {
   c->defer_n[1] = 0;
   c->defer_overflow = 0;
   c->holes_n = 0;
-  c->built = 0;
-  c->inserted = 0;
+  for (int i = 0; i < kLaunchKinds; ++i) c->built_k[i] = c->inserted_k[i] = 0;
   for (int i = 0; i < 8; ++i) c->work[i] = 0;
   c->sol = ~0ull;
 }
@@ -456,17 +455,17 @@ lsyn_status lsyn::ctx_commit_level(lsyn_ctx* c, int k, const DevCounters& h, uin
                                    unsigned long long deferred, const LevelPlan& lp, lsyn_level_stats* out) {
   const uint32_t start = lp.start;
   const uint32_t unique = total - start;
-  if (h.inserted != unique)
-    return c->fail(LSYN_E_STATE, "insert count " + std::to_string(h.inserted) + " differs from the level size " +
+  if (h.inserted() != unique)
+    return c->fail(LSYN_E_STATE, "insert count " + std::to_string(h.inserted()) + " differs from the level size " +
                                      std::to_string(unique));
   c->level_start.push_back(start);
   c->level_n.push_back(unique);
   c->levels_done = k;
   std::vector<int64_t> sizes(c->level_n.begin() + 1, c->level_n.end());
   const int64_t planned = k == 1 ? c->n_props : level_candidates(sizes.data(), k, c->op_mask);
-  const bool stopped = h.solved && c->full_levels == false && int64_t(h.built) < planned;
+  const bool stopped = h.solved && c->full_levels == false && int64_t(h.built()) < planned;
   c->last_incomplete = h.full || stopped;
-  c->constructed += h.built;
+  c->constructed += h.built();
   c->last_sol = h.solved ? h.sol : ~0ull;
   if (out) {
     memset(out, 0, sizeof(*out));
@@ -474,12 +473,12 @@ lsyn_status lsyn::ctx_commit_level(lsyn_ctx* c, int k, const DevCounters& h, uin
     out->solved = h.solved ? 1 : 0;
     out->cache_full = h.full ? 1 : 0;
     out->early_exit = stopped ? 1 : 0;
-    out->candidates = int64_t(h.built);
+    out->candidates = int64_t(h.built());
     out->unique = unique;
     out->total = total;
     out->deferred = int64_t(deferred);
     const double M = double(c->vecs) * 16.0;
-    const double C = double(h.built), U = double(unique);
+    const double C = double(h.built()), U = double(unique);
     // a level that stopped at a solution read only part of its operands
     const double done = planned > 0 ? std::min(1.0, C / double(planned)) : 1.0;
     out->bytes_alg = (lp.op_bytes_unary + lp.op_bytes_binary) * done + C * 32.0 + (C - U) * M + U * (M + 16.0);
@@ -741,10 +740,12 @@ lsyn_status lsyn_enumerate_level(lsyn_ctx* c, int32_t k, lsyn_level_stats* out) 
   ++launches;
   if ((e = cudaGetLastError()) != cudaSuccess) return c->cuda_fail(e, "level begin");
   ev_end(3);
-  if ((e = take_snap()) != cudaSuccess) return c->cuda_fail(e, "snapshot");  // snap 0: before work
 
+  // Each launch counts into its own kind of the level's counters
+  // (DevCounters::built_k / inserted_k), so the one read of the counters when
+  // the level closes gives every launch's share: no copy between launches.
   CacheView cv = c->view(c->defer[0], &c->ctr->defer_n[0]);
-  int binary_snap = -1, unary_snap = -1;
+  bool ran_unary = false, ran_binary = false;
   const double M = double(c->vecs) * 16.0;
   if (k == 1) {
     ev_begin();
@@ -752,26 +753,27 @@ lsyn_status lsyn_enumerate_level(lsyn_ctx* c, int32_t k, lsyn_level_stats* out) 
     ++launches;
     if (s != LSYN_OK) return s;
     ev_end(3);
-    if ((e = take_snap()) != cudaSuccess) return c->cuda_fail(e, "snapshot");
   } else {
     if (lp.uops && lp.u_count) {
+      CacheView uv = cv;
+      uv.kind = kKindUnary;
       ev_begin();
-      e = c->word_bits == 32 ? Kernels<uint32_t>::unary(cv, lp.u_first, lp.u_count, lp.uops, lc)
-                             : Kernels<uint64_t>::unary(cv, lp.u_first, lp.u_count, lp.uops, lc);
+      e = c->word_bits == 32 ? Kernels<uint32_t>::unary(uv, lp.u_first, lp.u_count, lp.uops, lc)
+                             : Kernels<uint64_t>::unary(uv, lp.u_first, lp.u_count, lp.uops, lc);
       ++launches;
       if (e != cudaSuccess) return c->cuda_fail(e, "unary kernel");
       ev_end(0);
-      if ((e = take_snap()) != cudaSuccess) return c->cuda_fail(e, "snapshot");
-      unary_snap = snap - 1;
+      ran_unary = true;
     }
     if (lp.plan.n_splits > 0) {
+      CacheView bv = cv;
+      bv.kind = kKindBinary;
       ev_begin();
-      e = c->word_bits == 32 ? Kernels<uint32_t>::binary(cv, lp.plan, lc) : Kernels<uint64_t>::binary(cv, lp.plan, lc);
+      e = c->word_bits == 32 ? Kernels<uint32_t>::binary(bv, lp.plan, lc) : Kernels<uint64_t>::binary(bv, lp.plan, lc);
       ++launches;
       if (e != cudaSuccess) return c->cuda_fail(e, "binary kernel");
       ev_end(1);
-      if ((e = take_snap()) != cudaSuccess) return c->cuda_fail(e, "snapshot");
-      binary_snap = snap - 1;
+      ran_binary = true;
     }
   }
   // Close the level without a host round trip in the common case: one pass
@@ -779,9 +781,10 @@ lsyn_status lsyn_enumerate_level(lsyn_ctx* c, int32_t k, lsyn_level_stats* out) 
   // hole plan + moves are queued behind the level's kernels, then read back
   // with one synchronisation. Candidates deferred again by that pass (rare)
   // are settled by host-driven passes, then the holes they left are closed.
-  const int main_snap = snap - 1;
-  auto pass = [&](int from, unsigned n) -> lsyn_status {  // re-examine list `from` into list 1 - from
-    if ((e = cudaMemsetAsync(&c->ctr->defer_n[1 - from], 0, sizeof(unsigned), c->stream)) != cudaSuccess)
+  // List 1 is empty when the level begins (k_level_begin), so the first pass
+  // needs no clear.
+  auto pass = [&](int from, unsigned n, bool clear) -> lsyn_status {  // list `from` into list 1 - from
+    if (clear && (e = cudaMemsetAsync(&c->ctr->defer_n[1 - from], 0, sizeof(unsigned), c->stream)) != cudaSuccess)
       return c->cuda_fail(e, "memset");
     CacheView rv = c->view(c->defer[1 - from], &c->ctr->defer_n[1 - from]);
     rv.early_exit = 0;  // a deferred candidate must be settled even after a solution
@@ -803,11 +806,11 @@ lsyn_status lsyn_enumerate_level(lsyn_ctx* c, int32_t k, lsyn_level_stats* out) 
     if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return c->cuda_fail(e, "level sync");
     return LSYN_OK;
   };
-  lsyn_status ls = pass(0, c->defer_cap);
+  lsyn_status ls = pass(0, c->defer_cap, false);
   if (ls != LSYN_OK) return ls;
-  if ((e = take_snap()) != cudaSuccess) return c->cuda_fail(e, "snapshot");
   if ((ls = close_holes()) != LSYN_OK) return ls;
-  unsigned long long deferred = std::min(c->h_snap[main_snap].c.defer_n[0], c->defer_cap);
+  // the pass reads list 0 and leaves its count as the level's kernels wrote it
+  unsigned long long deferred = std::min(c->h_snap[snap - 1].c.defer_n[0], c->defer_cap);
   int cur = 1;
   for (int npass = 1;; ++npass) {
     const DevCounters& h = c->h_snap[snap - 1].c;
@@ -819,7 +822,7 @@ lsyn_status lsyn_enumerate_level(lsyn_ctx* c, int32_t k, lsyn_level_stats* out) 
     if (n == 0) break;
     if (npass >= 48) return c->fail(LSYN_E_STATE, "deferred candidates did not settle");
     deferred += n;
-    if ((ls = pass(cur, n)) != LSYN_OK) return ls;
+    if ((ls = pass(cur, n, true)) != LSYN_OK) return ls;
     cur = 1 - cur;
     if ((e = take_snap()) != cudaSuccess) return c->cuda_fail(e, "snapshot");
     if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return c->cuda_fail(e, "resolve sync");
@@ -847,17 +850,15 @@ lsyn_status lsyn_enumerate_level(lsyn_ctx* c, int32_t k, lsyn_level_stats* out) 
     // slot per insert.
     // a launch that stopped at a solution read its operands only in part: in
     // proportion to the candidates it built
-    auto launch_bytes = [&](int sn, double operands, double planned) {
-      const DevCounters& b0 = c->h_snap[sn - 1].c;
-      const DevCounters& b1 = c->h_snap[sn].c;
-      const double Cl = double(b1.built - b0.built);
-      const double Ul = double(b1.inserted - b0.inserted);
+    auto launch_bytes = [&](unsigned kind, double operands, double planned) {
+      const double Cl = double(h.built_k[kind]);
+      const double Ul = double(h.inserted_k[kind]);
       const double done = planned > 0 ? std::min(1.0, Cl / planned) : 1.0;
       return operands * done + Cl * 32.0 + (Cl - Ul) * M + Ul * (M + 16.0);
     };
     const double planned = double(level_candidate_count(c, k) > 0 ? level_candidate_count(c, k) : 0);
-    if (binary_snap >= 0) out->bytes_binary = launch_bytes(binary_snap, lp.op_bytes_binary, planned - lp.cand_unary);
-    if (unary_snap >= 0) out->bytes_unary = launch_bytes(unary_snap, lp.op_bytes_unary, lp.cand_unary);
+    if (ran_binary) out->bytes_binary = launch_bytes(kKindBinary, lp.op_bytes_binary, planned - lp.cand_unary);
+    if (ran_unary) out->bytes_unary = launch_bytes(kKindUnary, lp.op_bytes_unary, lp.cand_unary);
     if (c->timing) {
       for (int i = 0; i < evn; ++i) {
         float ms = 0;

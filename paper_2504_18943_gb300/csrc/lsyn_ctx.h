@@ -190,6 +190,7 @@ struct lsyn_ctx {
     cv.planes = planes;
     cv.plane_vecs = plane_vecs;
     cv.time_budget_ns = level_budget_ns;
+    cv.kind = lsyn::kKindOther;
     return cv;
   }
 };

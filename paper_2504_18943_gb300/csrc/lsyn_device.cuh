@@ -512,8 +512,8 @@ __global__ void __launch_bounds__(256) k_unary_a(CacheView cv, uint32_t first, u
       ++built;
     }
   }
-  if (built) atomicAdd(&cv.ctr->built, built);
-  if (ins) atomicAdd(&cv.ctr->inserted, ins);
+  if (built) atomicAdd(&cv.ctr->built_k[cv.kind], built);
+  if (ins) atomicAdd(&cv.ctr->inserted_k[cv.kind], ins);
 }
 
 template <typename W, int V>
@@ -541,8 +541,8 @@ __global__ void __launch_bounds__(256) k_binary_a(CacheView cv, BinaryPlan plan)
     if (plan.ops & 4u) { ins += P::candidate(cv, s, kUntil, a, b, pack_desc(kUntil, a_id, b_id), full); ++built; }
     if (plan.ops & 8u) { ins += P::candidate(cv, s, kUntil, b, a, pack_desc(kUntil, b_id, a_id), full); ++built; }
   }
-  if (built) atomicAdd(&cv.ctr->built, built);
-  if (ins) atomicAdd(&cv.ctr->inserted, ins);
+  if (built) atomicAdd(&cv.ctr->built_k[cv.kind], built);
+  if (ins) atomicAdd(&cv.ctr->inserted_k[cv.kind], ins);
 }
 
 // Rebuild a candidate from its descriptor (operands are complete levels).
@@ -583,8 +583,8 @@ __global__ void __launch_bounds__(256) k_desc_a(CacheView cv, const unsigned lon
     rebuild_a<W, V>(cv, s, d, c);
     ins += P::process(cv, s, c, d, ld_relaxed_u32(&cv.ctr->full) != 0u);
   }
-  if (ins) atomicAdd(&cv.ctr->inserted, ins);
-  if (implicit_atoms && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&cv.ctr->built, (unsigned long long)n);
+  if (ins) atomicAdd(&cv.ctr->inserted_k[cv.kind], ins);
+  if (implicit_atoms && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&cv.ctr->built_k[cv.kind], (unsigned long long)n);
 }
 
 // ===========================================================================
@@ -680,7 +680,7 @@ struct WarpDedup {
     if (lane == 0) {
       log_hole(cv, ids.next, ids.end);
       if (ids.pre_ok) log_hole(cv, ids.pre, ids.pre + cv.chunk);
-      if (ids.inserted) atomicAdd(&cv.ctr->inserted, ids.inserted);
+      if (ids.inserted) atomicAdd(&cv.ctr->inserted_k[cv.kind], ids.inserted);
     }
     ids.next = ids.end = 0;
     ids.pre_ok = false;
@@ -962,14 +962,21 @@ struct UnaryGen {
 template <typename W>
 struct ListGen {
   const CacheView* cv;
-  const uint64_t* d;  // shared memory: the group's descriptors
+  const uint64_t* d;  // shared memory: the batch's descriptors
+  uint4* keep;        // shared memory: this lane's vector of candidate q at keep[q * 32 + lane]
   uint4 lm;
   int lane;
+  // The batch's hash pass computes every candidate (in groups of four, in
+  // order) before any compute(q): each candidate's operands are read once and
+  // its vector kept for the compare and write passes.
   __device__ void compute4(int q0, uint4 (&c)[4]) const {
 #pragma unroll
-    for (int o = 0; o < 4; ++o) c[o] = compute(q0 + o);
+    for (int o = 0; o < 4; ++o) c[o] = build(q0 + o);
+#pragma unroll
+    for (int o = 0; o < 4; ++o) keep[(q0 + o) * 32 + lane] = c[o];
   }
-  __device__ uint4 compute(int q) const {
+  __device__ uint4 compute(int q) const { return keep[q * 32 + lane]; }
+  __device__ uint4 build(int q) const {
     const uint64_t dd = d[q];
     const uint32_t op = desc_op(dd);
     if (op == kAtom) return __ldg(cv->atoms + size_t(desc_left(dd)) * cv->vecs + lane);
@@ -1025,7 +1032,7 @@ __global__ void __launch_bounds__(256, 3) k_unary_c(CacheView cv, uint32_t first
   }
   WarpDedup::flush(pend);
   WarpDedup::retire(cv, idr);
-  if (lane == 0 && built) atomicAdd(&cv.ctr->built, built);
+  if (lane == 0 && built) atomicAdd(&cv.ctr->built_k[cv.kind], built);
 }
 
 template <typename W>
@@ -1100,7 +1107,7 @@ __global__ void __launch_bounds__(256, 4) k_binary_c(CacheView cv, BinaryPlan pl
   }
   WarpDedup::flush(pend);
   WarpDedup::retire(cv, idr);
-  if (lane == 0 && built) atomicAdd(&cv.ctr->built, built);
+  if (lane == 0 && built) atomicAdd(&cv.ctr->built_k[cv.kind], built);
 }
 
 // Splits whose smaller level has fewer than kSmallSplitRows rows (the atoms
@@ -1167,24 +1174,32 @@ __global__ void __launch_bounds__(256, 3) k_binary_small_c(CacheView cv, BinaryP
   }
   WarpDedup::flush(pend);
   WarpDedup::retire(cv, idr);
-  if (lane == 0 && built) atomicAdd(&cv.ctr->built, built);
+  if (lane == 0 && built) atomicAdd(&cv.ctr->built_k[cv.kind], built);
 }
 
+// Candidates per warp batch of k_desc_c. A deferred candidate is built from
+// its descriptor's operand rows in global memory, one round trip per group of
+// four; small batches keep that chain short and spread a short list (the
+// usual case) over many warps.
+constexpr int kDescBatch = 8;
+
 template <typename W>
-__global__ void __launch_bounds__(256, 4) k_desc_c(CacheView cv, const unsigned long long* list,
+__global__ void __launch_bounds__(256, 3) k_desc_c(CacheView cv, const unsigned long long* list,
                                                    const unsigned int* list_n, unsigned int list_cap,
                                                    unsigned int implicit_atoms) {
   using P = PathC<W>;
-  constexpr int N = 32;
+  constexpr int N = kDescBatch;
   extern __shared__ uint4 smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  uint4* stage = smem + wib * (P::kStage + N / 2);
-  uint64_t* dbuf = reinterpret_cast<uint64_t*>(stage + P::kStage);  // N descriptors
+  uint4* stage = smem + wib * (P::kStage + N * 32 + N / 2);
+  uint4* keep = stage + P::kStage;
+  uint64_t* dbuf = reinterpret_cast<uint64_t*>(keep + N * 32);  // N descriptors
   typename P::Consts k;
   P::load_consts(cv, k);
   ListGen<W> gen;
   gen.cv = &cv;
   gen.d = dbuf;
+  gen.keep = keep;
   gen.lm = cv.lenmask[lane];
   gen.lane = lane;
   const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -1198,15 +1213,14 @@ __global__ void __launch_bounds__(256, 4) k_desc_c(CacheView cv, const unsigned 
     const uint32_t cnt = min(uint32_t(N), n - base);
     // descriptors past cnt (up to a multiple of 4) are harmless atoms, disabled by `en`
     if (lane < int(cnt)) dbuf[lane] = list ? list[base + lane] : pack_desc(kAtom, base + lane, 0);
-    else dbuf[lane] = pack_desc(kAtom, 0, 0);
+    else if (lane < N) dbuf[lane] = pack_desc(kAtom, 0, 0);
     __syncwarp();
-    P::template batch<false>(cv, k, gen, int((cnt + 3u) & ~3u), cnt >= 32u ? 0xFFFFFFFFu : ((1u << cnt) - 1u),
-                             stage, pend, idr);
+    P::template batch<false>(cv, k, gen, int((cnt + 3u) & ~3u), (1u << cnt) - 1u, stage, pend, idr);
     __syncwarp();
   }
   WarpDedup::flush(pend);
   WarpDedup::retire(cv, idr);
-  if (implicit_atoms && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&cv.ctr->built, (unsigned long long)n);
+  if (implicit_atoms && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&cv.ctr->built_k[cv.kind], (unsigned long long)n);
 }
 
 // ===========================================================================
@@ -1523,7 +1537,7 @@ __global__ void __launch_bounds__(256) k_unary_d(CacheView cv, uint32_t first, u
   }
   WarpDedup::flush(pend);
   WarpDedup::retire(cv, idr);
-  if (lane == 0 && built) atomicAdd(&cv.ctr->built, built);
+  if (lane == 0 && built) atomicAdd(&cv.ctr->built_k[cv.kind], built);
 }
 
 // Pairs of every split in one flat index space (as path A), 8 per warp batch.
@@ -1571,7 +1585,7 @@ __global__ void __launch_bounds__(256) k_binary_d(CacheView cv, BinaryPlan plan)
   }
   WarpDedup::flush(pend);
   WarpDedup::retire(cv, idr);
-  if (lane == 0 && built) atomicAdd(&cv.ctr->built, built);
+  if (lane == 0 && built) atomicAdd(&cv.ctr->built_k[cv.kind], built);
 }
 
 template <typename W>
@@ -1601,7 +1615,7 @@ __global__ void __launch_bounds__(256) k_desc_d(CacheView cv, const unsigned lon
   }
   WarpDedup::flush(pend);
   WarpDedup::retire(cv, idr);
-  if (implicit_atoms && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&cv.ctr->built, (unsigned long long)n);
+  if (implicit_atoms && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&cv.ctr->built_k[cv.kind], (unsigned long long)n);
 }
 
 // ===========================================================================
@@ -1644,7 +1658,7 @@ struct BatchWarp {
     if (cur < 0) return;
     WarpDedup::flush(pend);
     WarpDedup::retire(*s_cv, ids);
-    if ((threadIdx.x & 31) == 0 && built) atomicAdd(&s_cv->ctr->built, built);
+    if ((threadIdx.x & 31) == 0 && built) atomicAdd(&s_cv->ctr->built_k[s_cv->kind], built);
     built = 0;
     __syncwarp();
     cur = -1;
@@ -1825,8 +1839,7 @@ static __global__ void k_batch_begin(StepHeader* hdr, const StepProblem* steps, 
   c->defer_n[1] = 0;
   c->defer_overflow = 0;
   c->holes_n = 0;
-  c->built = 0;
-  c->inserted = 0;
+  for (int i = 0; i < kLaunchKinds; ++i) c->built_k[i] = c->inserted_k[i] = 0;
   c->sol = ~0ull;
   c->timed_out = 0;
   for (int i = 0; i < 8; ++i) c->work[i] = 0;  // tile counters of one-problem launches in the step
@@ -1866,28 +1879,55 @@ static __global__ void k_batch_set_entries(const StepProblem* steps, const unsig
 
 // ===========================================================================
 // Hole fixup: after a level, move the entries that lie above the level's dense
-// end into the holes below it (one warp per move): copy the CM row, its
-// provenance and slot index, and repoint the table slot to the new id.
+// end into the holes below it: copy the CM row, its provenance and slot index,
+// and repoint the table slot to the new id. A warp takes kFixupMoves moves at
+// a time with their loads in flight together (a move is a chain of dependent
+// loads: the move, the row or the slot index, the slot). Sources lie at or
+// above the dense end and destinations below it, so the moves are disjoint.
 // ===========================================================================
+constexpr int kFixupMoves = 4;
+
 static __global__ void __launch_bounds__(256) k_fixup(CacheView cv, const uint2* moves, unsigned n,
                                                       const unsigned* n_dev) {
+  constexpr int G = kFixupMoves;
   const int lane = threadIdx.x & 31;
   const unsigned warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
   if (n_dev) n = *n_dev;  // planned on the device (k_hole_plan)
-  for (unsigned m = warp; m < n; m += nwarps) {
-    const unsigned src = moves[m].x, dst = moves[m].y;
-    const uint4* a = cv.arena + size_t(src) * cv.vecs;
-    uint4* b = cv.arena + size_t(dst) * cv.vecs;
-    for (unsigned v = lane; v < cv.vecs; v += 32) b[v] = a[v];
-    if (lane == 1) cv.prov[dst] = cv.prov[src];
-    if (lane == 2) cv.homes[dst] = cv.homes[src];
-    if (lane == 0) {
-      const unsigned sp = cv.slotpos[src];
-      cv.slotpos[dst] = sp;
-      const unsigned long long old = cv.table[sp];
-      if (uint32_t(old) == src + 1u) cv.table[sp] = (old & 0xFFFFFFFF00000000ull) | (unsigned long long)(dst + 1u);
-      else atomicExch(&cv.ctr->error, 3u);
+  for (unsigned m0 = warp * G; m0 < n; m0 += nwarps * G) {
+    const unsigned g = min(unsigned(G), n - m0);
+    uint2 mv[G];
+#pragma unroll
+    for (int j = 0; j < G; ++j) mv[j] = j < int(g) ? moves[m0 + j] : make_uint2(0u, 0u);
+    for (unsigned v0 = 0; v0 < cv.vecs; v0 += 32) {
+      const unsigned v = v0 + unsigned(lane);
+      uint4 t[G];
+#pragma unroll
+      for (int j = 0; j < G; ++j)
+        if (j < int(g) && v < cv.vecs) t[j] = cv.arena[size_t(mv[j].x) * cv.vecs + v];
+#pragma unroll
+      for (int j = 0; j < G; ++j)
+        if (j < int(g) && v < cv.vecs) cv.arena[size_t(mv[j].y) * cv.vecs + v] = t[j];
+    }
+    // lane j: provenance, lane G + j: hash home, lane 2G + j: slot of move j
+    const int j = lane % G, role = lane / G;
+    if (j < int(g)) {
+      unsigned src = 0, dst = 0;  // mv[j], selected in registers
+#pragma unroll
+      for (int q = 0; q < G; ++q)
+        if (q == j) {
+          src = mv[q].x;
+          dst = mv[q].y;
+        }
+      if (role == 0) cv.prov[dst] = cv.prov[src];
+      else if (role == 1) cv.homes[dst] = cv.homes[src];
+      else if (role == 2) {
+        const unsigned sp = cv.slotpos[src];
+        cv.slotpos[dst] = sp;
+        const unsigned long long old = cv.table[sp];
+        if (uint32_t(old) == src + 1u) cv.table[sp] = (old & 0xFFFFFFFF00000000ull) | (unsigned long long)(dst + 1u);
+        else atomicExch(&cv.ctr->error, 3u);
+      }
     }
   }
 }
@@ -1988,12 +2028,22 @@ static __global__ void __launch_bounds__(1024) k_hole_plan(DevCounters* ctr, con
   unsigned* bits = sc.bits();
   for (unsigned w = t; w < words; w += T) bits[w] = 0u;
   __syncthreads();
-  // 2. the holes at or above the dense end, as a bitmap of [dense_end, total)
+  // 2. the holes at or above the dense end, as a bitmap of [dense_end, total):
+  // one masked OR per bitmap word a range touches (two at most), not one per
+  // id (the top of a level's range is mostly holes, and the ORs of one block
+  // are served one after another)
 #pragma unroll 8
   for (unsigned i = t; i < n; i += T) {
     const uint2 r = holes[i];
     const unsigned lo = max(max(r.x, start), dense_end), hi = min(r.y, total);
-    for (unsigned id = lo; id < hi; ++id) atomicOr(&bits[(id - dense_end) >> 5], 1u << ((id - dense_end) & 31u));
+    if (lo >= hi) continue;
+    unsigned a = lo - dense_end;
+    const unsigned b = hi - dense_end;
+    while (a < b) {
+      const unsigned o = a & 31u, nb = min(32u - o, b - a);
+      atomicOr(&bits[a >> 5], (nb == 32u ? 0xFFFFFFFFu : ((1u << nb) - 1u)) << o);
+      a += nb;
+    }
   }
   __syncthreads();
   // 3. live entries before each bitmap word (contiguous words per thread)
@@ -2049,9 +2099,12 @@ static __global__ void __launch_bounds__(1024) k_hole_plan(DevCounters* ctr, con
   }
 }
 
-// Moves: thread per rank r < moves_n. The source is the r-th live entry of
-// [dense_end, total), the destination the r-th hole id below dense_end; both
-// are found by binary search over the plan's prefix arrays.
+// Moves, by scatter: the r-th live entry of [dense_end, total) is the source
+// and the r-th hole id below dense_end the destination of move r. Items
+// 0 .. words-1 are the bitmap words (each writes the sources of its live
+// entries from the word's prefix), items words .. words+n-1 the logged ranges
+// (each writes the destinations of its ids below dense_end from the range's
+// prefix). Sources fill moves[r].x and destinations moves[r].y.
 static __global__ void __launch_bounds__(256) k_hole_moves(const DevCounters* ctr, const uint2* holes,
                                                            unsigned start, HoleScratch sc, uint2* moves) {
   const unsigned m = ctr->moves_n;
@@ -2061,25 +2114,19 @@ static __global__ void __launch_bounds__(256) k_hole_moves(const DevCounters* ct
   const unsigned* bits = sc.bits();
   const unsigned* wp = sc.word_pref();
   const unsigned* rp = sc.range_pref();
-  for (unsigned r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x) {
-    // last word w with wp[w] <= r (wp[0] = 0 <= r, wp[words] = m > r)
-    unsigned lo = 0, hi = words;
-    while (hi - lo > 1u) {
-      const unsigned mid = (lo + hi) >> 1;
-      if (__ldcg(wp + mid) <= r) lo = mid; else hi = mid;
+  unsigned* out = reinterpret_cast<unsigned*>(moves);
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < words + n; i += gridDim.x * blockDim.x) {
+    if (i < words) {
+      unsigned live = hole_live_word(bits, i, words, H);
+      unsigned r = __ldcg(wp + i);
+      for (; live && r < m; live &= live - 1u, ++r) out[2 * size_t(r)] = dense_end + i * 32u + unsigned(__ffs(live) - 1);
+    } else {
+      const unsigned h = i - words;
+      const uint2 rg = holes[h];
+      const unsigned lo = max(rg.x, start), hi = min(min(rg.y, dense_end + H), dense_end);
+      unsigned r = __ldcg(rp + h);
+      for (unsigned id = lo; id < hi && r < m; ++id, ++r) out[2 * size_t(r) + 1] = id;
     }
-    unsigned live = hole_live_word(bits, lo, words, H);
-    for (unsigned k = r - __ldcg(wp + lo); k; --k) live &= live - 1u;
-    const unsigned src = dense_end + lo * 32u + unsigned(__ffs(live) - 1);
-    // last range i with rp[i] <= r (rp[0] = 0 <= r, rp[n] = m > r)
-    lo = 0;
-    hi = n;
-    while (hi - lo > 1u) {
-      const unsigned mid = (lo + hi) >> 1;
-      if (__ldcg(rp + mid) <= r) lo = mid; else hi = mid;
-    }
-    const unsigned dst = max(holes[lo].x, start) + (r - __ldcg(rp + lo));
-    moves[r] = make_uint2(src, dst);
   }
 }
 
@@ -2207,12 +2254,18 @@ struct LaunchA {
 template <typename W>
 struct LaunchC {
   static constexpr size_t kUnarySmem = size_t(8) * (kUnaryRowsC * 32 + PathC<W>::kStage) * sizeof(uint4);
-  static constexpr size_t kDescSmem = size_t(8) * (PathC<W>::kStage + 16) * sizeof(uint4);
+  static constexpr size_t kDescSmem =
+      size_t(8) * (PathC<W>::kStage + kDescBatch * 32 + kDescBatch / 2) * sizeof(uint4);
   static constexpr size_t kStageSmem = size_t(8) * PathC<W>::kStage * sizeof(uint4);
   static cudaError_t desc_list(const CacheView& cv, const unsigned long long* list, const unsigned int* list_n,
                                unsigned int cap, unsigned int atoms, const LaunchCfg& lc) {
+    static bool once = (cudaFuncSetAttribute((const void*)k_desc_c<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             int(kDescSmem)), true);
+    (void)once;
+    static int occ = occupancy_blocks((const void*)k_desc_c<W>, 256, kDescSmem);
     const unsigned n = list ? cap : atoms;
-    const unsigned blocks = std::max(1u, std::min((n + 255u) / 256u, unsigned(lc.sms * 4)));
+    const unsigned per_block = 8u * unsigned(kDescBatch);
+    const unsigned blocks = std::max(1u, std::min((n + per_block - 1u) / per_block, unsigned(lc.sms * occ)));
     k_desc_c<W><<<blocks, 256, kDescSmem, lc.stream>>>(cv, list, list_n, cap, atoms);
     return cudaGetLastError();
   }
@@ -2402,7 +2455,8 @@ cudaError_t Kernels<W>::rehash(const unsigned long long* old_t, unsigned long lo
 template <typename W>
 cudaError_t Kernels<W>::fixup(const CacheView& cv, const uint2* moves, unsigned n, const LaunchCfg& lc) {
   if (n == 0) return cudaSuccess;
-  const unsigned blocks = std::max(1u, std::min((n + 7u) / 8u, unsigned(lc.sms * 8)));
+  const unsigned per_block = 8u * unsigned(kFixupMoves);
+  const unsigned blocks = std::max(1u, std::min((n + per_block - 1u) / per_block, unsigned(lc.sms * 8)));
   k_fixup<<<blocks, 256, 0, lc.stream>>>(cv, moves, n, nullptr);
   return cudaGetLastError();
 }

@@ -906,7 +906,7 @@ lsyn_status Engine::run_group(std::vector<Plan>& g, int word_bits, int sms) {
   if (s != LSYN_OK) return s;
   cur_.run_ms += now_ms() - tr;
   cur_.active += n;
-  for (const Plan& p : g) cur_.candidates += h_ctrs_[p.j->slot].built;
+  for (const Plan& p : g) cur_.candidates += h_ctrs_[p.j->slot].built();
 
   // 2. deferred candidates of every job, one launch per pass
   for (int pass = 0;; ++pass) {
@@ -1191,7 +1191,7 @@ lsyn_status Engine::lane_advance(Lane& L, bool* progressed) {
   if (!L.ran) {
     L.ran = true;
     L.rec.run_ms = now_ms() - L.t_launched;
-    L.rec.candidates = h.built;
+    L.rec.candidates = h.built();
   }
   cudaError_t e = cudaSuccess;
   switch (L.stage) {

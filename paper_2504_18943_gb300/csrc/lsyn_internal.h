@@ -42,6 +42,12 @@ constexpr uint32_t kSlotTomb = 0xFFFFFFFEu;     // claimed, but the arena was fu
 // the flags and (rarely) appends to the deferred list, and operations on one
 // line are served one after another at one L2 slice, so a flag that shared the
 // counter's line waited behind its atomics.
+// Kinds of launch whose counts are kept apart: the unary and the binary
+// operators of a level, and everything else (atoms, deferred re-examination,
+// the batch kernels).
+constexpr int kLaunchKinds = 4;
+constexpr unsigned kKindUnary = 0, kKindBinary = 1, kKindOther = 2;
+
 struct alignas(128) DevCounters {
   // ---- the id counter (an atomic per warp chunk) ----
   unsigned int n_entries;        // arena fill (may exceed max_entries when full)
@@ -61,10 +67,22 @@ struct alignas(128) DevCounters {
   unsigned int holes_n;          // id ranges reserved but left unused (hole log fill)
   unsigned int pad2[28];
   // ---- per-level totals (an atomic per warp at exit) and the hole plan ----
-  unsigned long long built;      // candidates built in this level
-  unsigned long long inserted;   // new entries written in this level
+  // Split by the kind of launch that counted them (CacheView::kind), so that
+  // one read of the counters after a level gives every launch's share.
+  unsigned long long built_k[kLaunchKinds];     // candidates built in this level
+  unsigned long long inserted_k[kLaunchKinds];  // new entries written in this level
   unsigned int moves_n;          // hole moves planned on the device (k_hole_plan)
-  unsigned int pad3[27];
+  unsigned int pad3[15];
+  __host__ __device__ unsigned long long built() const {
+    unsigned long long t = 0;
+    for (int i = 0; i < kLaunchKinds; ++i) t += built_k[i];
+    return t;
+  }
+  __host__ __device__ unsigned long long inserted() const {
+    unsigned long long t = 0;
+    for (int i = 0; i < kLaunchKinds; ++i) t += inserted_k[i];
+    return t;
+  }
   // ---- tile counters of the persistent launches ----
   unsigned long long work[8];
   unsigned int pad4[16];
@@ -99,6 +117,7 @@ struct CacheView {
   unsigned int planes;           // words per trace: plane j holds positions [j w, (j + 1) w) of every trace
   unsigned int plane_vecs;       // vectors of one plane (vecs = planes x plane_vecs, then padding)
   unsigned long long time_budget_ns;  // 0: none; else stop once the global timer passes ctr->t0 + this
+  unsigned int kind;             // which DevCounters::built_k / inserted_k this launch counts into
 };
 
 // One split {i, j} of level k (i + j = k - 1) for the binary operators.
