@@ -1512,10 +1512,23 @@ struct ListGenD {
   __device__ uint64_t desc(int q) const { return d[q]; }
 };
 
+// Rows of level k-1 per warp batch of k_unary_d (4 operators each). A batch
+// reads its rows once to hash them and again to compare or write its
+// candidates; one 16 KiB row per warp keeps the rows of all resident warps
+// in L2 between the passes (8 rows per warp did not fit, and the second reads
+// went to DRAM), and a batch's round trips stay short beside its streaming.
+constexpr int kRowsD = 1;
+// Vectors per lane computed together in the hash pass of path D: of k_unary_d
+// (one row read, four loads in flight per lane), and of k_binary_d and
+// k_desc_d. Measured at 16 KiB CMs: 4 against 1, 2 or 8 for the unary
+// kernel, 2 against 1 or 4 for the binary one.
+constexpr int kVptUnaryD = 4;
+constexpr int kVptD = 2;
+
 template <typename W>
 __global__ void __launch_bounds__(256) k_unary_d(CacheView cv, uint32_t first, uint32_t count, uint32_t ops) {
-  using P = PathD<W>;
-  constexpr int ROWS = 8;
+  using P = PathD<W, kVptUnaryD>;
+  constexpr int ROWS = kRowsD;
   const int lane = threadIdx.x & 31;
   RowGenD<W> gen;
   gen.cv = &cv;
@@ -1540,11 +1553,15 @@ __global__ void __launch_bounds__(256) k_unary_d(CacheView cv, uint32_t first, u
   if (lane == 0 && built) atomicAdd(&cv.ctr->built_k[cv.kind], built);
 }
 
-// Pairs of every split in one flat index space (as path A), 8 per warp batch.
+// Pairs of every split in one flat index space (as path A), kPairsD per warp
+// batch (4 measured faster than 8, 2 or 1 at 16 KiB CMs).
+constexpr int kPairsD = 4;
+
 template <typename W>
 __global__ void __launch_bounds__(256) k_binary_d(CacheView cv, BinaryPlan plan) {
-  using P = PathD<W>;
-  __shared__ uint2 s_pairs[8][8];
+  using P = PathD<W, kVptD>;
+  constexpr int PAIRS = kPairsD;
+  __shared__ uint2 s_pairs[8][PAIRS];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   PairGenD<W> gen;
   gen.cv = &cv;
@@ -1554,11 +1571,11 @@ __global__ void __launch_bounds__(256) k_binary_d(CacheView cv, BinaryPlan plan)
   unsigned long long built = 0;
   typename P::Pending pend;
   typename P::Ids idr;
-  for (unsigned long long g0 = warp * 8; g0 < plan.total_pairs; g0 += nwarps * 8) {
+  for (unsigned long long g0 = warp * PAIRS; g0 < plan.total_pairs; g0 += nwarps * PAIRS) {
     if (__any_sync(kFull, stop_requested(cv))) break;
-    // lane p < 8 maps pair g0 + p to its operands
+    // lane p < PAIRS maps pair g0 + p to its operands
     uint32_t ok = 0;
-    if (lane < 8) {
+    if (lane < PAIRS) {
       const unsigned long long pidx = g0 + lane;
       bool valid = pidx < plan.total_pairs;
       uint2 pr = make_uint2(0, 0);
@@ -1572,13 +1589,13 @@ __global__ void __launch_bounds__(256) k_binary_d(CacheView cv, BinaryPlan plan)
       s_pairs[wib][lane] = pr;
       ok = valid ? 1u : 0u;
     }
-    const uint32_t pv = __ballot_sync(kFull, ok != 0u) & 0xFFu;
+    const uint32_t pv = __ballot_sync(kFull, ok != 0u) & ((1u << PAIRS) - 1u);
     __syncwarp();
     uint32_t en = 0;
 #pragma unroll
-    for (int q = 0; q < 32; ++q) en |= (((pv >> (q >> 2)) & 1u) & ((plan.ops >> (q & 3)) & 1u)) << q;
+    for (int q = 0; q < 4 * PAIRS; ++q) en |= (((pv >> (q >> 2)) & 1u) & ((plan.ops >> (q & 3)) & 1u)) << q;
     if (en) {
-      P::template batch<true>(cv, gen, 32, en, pend, idr);
+      P::template batch<true>(cv, gen, 4 * PAIRS, en, pend, idr);
       built += __popc(en);
     }
     __syncwarp();
@@ -1592,7 +1609,7 @@ template <typename W>
 __global__ void __launch_bounds__(256) k_desc_d(CacheView cv, const unsigned long long* list,
                                                 const unsigned int* list_n, unsigned int list_cap,
                                                 unsigned int implicit_atoms) {
-  using P = PathD<W>;
+  using P = PathD<W, kVptD>;
   __shared__ uint64_t s_d[8][32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   ListGenD<W> gen;
