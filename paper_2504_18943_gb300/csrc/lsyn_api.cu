@@ -757,6 +757,14 @@ lsyn_status lsyn_enumerate_level(lsyn_ctx* c, int32_t k, lsyn_level_stats* out) 
     if (lp.uops && lp.u_count) {
       CacheView uv = cv;
       uv.kind = kKindUnary;
+      // CMs above 512 bytes (path D): a unary batch (one row, four candidates)
+      // streams tens of microseconds of rows, so one id reservation per batch
+      // is cheap beside it, while every id a warp leaves unused costs a row
+      // move (2 M bytes) when the level closes: reserve exactly the batch's
+      // inserts (and no prefetched chunk). The binary kernel's shorter
+      // batches keep their chunks: a reservation per batch slowed it more
+      // than its holes cost.
+      if (c->vecs > 32u) uv.chunk = 1;
       ev_begin();
       e = c->word_bits == 32 ? Kernels<uint32_t>::unary(uv, lp.u_first, lp.u_count, lp.uops, lc)
                              : Kernels<uint64_t>::unary(uv, lp.u_first, lp.u_count, lp.uops, lc);
@@ -788,6 +796,7 @@ lsyn_status lsyn_enumerate_level(lsyn_ctx* c, int32_t k, lsyn_level_stats* out) 
       return c->cuda_fail(e, "memset");
     CacheView rv = c->view(c->defer[1 - from], &c->ctr->defer_n[1 - from]);
     rv.early_exit = 0;  // a deferred candidate must be settled even after a solution
+    if (c->vecs > 32u) rv.chunk = 1;  // as the unary kernel's (path D)
     ev_begin();
     lsyn_status s = launch_desc(c, rv, c->defer[from], &c->ctr->defer_n[from], n, 0, lc);
     ++launches;

@@ -1605,12 +1605,19 @@ __global__ void __launch_bounds__(256) k_binary_d(CacheView cv, BinaryPlan plan)
   if (lane == 0 && built) atomicAdd(&cv.ctr->built_k[cv.kind], built);
 }
 
+// Descriptors per warp batch of k_desc_d: one group of four. A path-D batch
+// walks its groups one after another, each a chain of passes over the
+// candidates' vectors, so a short deferred list (the usual case) spreads over
+// many warps instead of queueing in a few.
+constexpr int kDescBatchD = 4;
+
 template <typename W>
 __global__ void __launch_bounds__(256) k_desc_d(CacheView cv, const unsigned long long* list,
                                                 const unsigned int* list_n, unsigned int list_cap,
                                                 unsigned int implicit_atoms) {
   using P = PathD<W, kVptD>;
-  __shared__ uint64_t s_d[8][32];
+  constexpr int N = kDescBatchD;
+  __shared__ uint64_t s_d[8][N];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   ListGenD<W> gen;
   gen.cv = &cv;
@@ -1621,13 +1628,14 @@ __global__ void __launch_bounds__(256) k_desc_d(CacheView cv, const unsigned lon
   if (list) n = min(*list_n, list_cap);
   typename P::Pending pend;
   typename P::Ids idr;
-  for (uint32_t base = warp * 32; base < n; base += nwarps * 32) {
+  for (uint32_t base = warp * N; base < n; base += nwarps * N) {
     if (__any_sync(kFull, stop_requested(cv))) break;
-    const uint32_t cnt = min(32u, n - base);
-    s_d[wib][lane] = lane < int(cnt) ? (list ? list[base + lane] : pack_desc(kAtom, base + lane, 0))
-                                     : pack_desc(kAtom, 0, 0);
+    const uint32_t cnt = min(uint32_t(N), n - base);
+    if (lane < N)
+      s_d[wib][lane] = lane < int(cnt) ? (list ? list[base + lane] : pack_desc(kAtom, base + lane, 0))
+                                       : pack_desc(kAtom, 0, 0);
     __syncwarp();
-    P::template batch<false>(cv, gen, int(cnt), cnt >= 32u ? 0xFFFFFFFFu : ((1u << cnt) - 1u), pend, idr);
+    P::template batch<false>(cv, gen, int(cnt), (1u << cnt) - 1u, pend, idr);
     __syncwarp();
   }
   WarpDedup::flush(pend);
@@ -2376,8 +2384,10 @@ template <typename W>
 struct LaunchD {
   static cudaError_t desc_list(const CacheView& cv, const unsigned long long* list, const unsigned int* list_n,
                                unsigned int cap, unsigned int atoms, const LaunchCfg& lc) {
+    static int occ = occupancy_blocks((const void*)k_desc_d<W>, 256, 0);
     const unsigned n = list ? cap : atoms;
-    const unsigned blocks = std::max(1u, std::min((n + 255u) / 256u, unsigned(lc.sms * 8)));
+    const unsigned per_block = 8u * unsigned(kDescBatchD);
+    const unsigned blocks = std::max(1u, std::min((n + per_block - 1u) / per_block, unsigned(lc.sms * occ)));
     k_desc_d<W><<<blocks, 256, 0, lc.stream>>>(cv, list, list_n, cap, atoms);
     return cudaGetLastError();
   }
