@@ -33,7 +33,9 @@
  *    before returning (outputs). The caller keeps ownership.
  *  - Device memory is owned by the context and released by lsyn_destroy().
  *  - One context is used by one host thread at a time. All device work of a
- *    context is issued on the stream given in lsyn_config.
+ *    context is issued on the stream given in lsyn_config, except the clear of
+ *    a large hash table after lsyn_reset, which runs on a stream of the
+ *    context's own, ordered by events (see lsyn_reset).
  *  - Formula text: prefix, fully parenthesised, atoms p0..p{n-1}, e.g.
  *    "(U (! p1) (& p0 (X p1)))". Unary: "(! f)", "(X f)", "(F f)", "(G f)";
  *    binary: "(& f g)", "(| f g)", "(U f g)".
@@ -226,7 +228,17 @@ void lsyn_destroy(lsyn_ctx* ctx);
 /* Message of the last error on this context; with NULL, of the last failed lsyn_create on this thread. */
 const char* lsyn_last_error(const lsyn_ctx* ctx);
 
-/* Forget every level (keeps the traces and the memory); the next level to build is 1. */
+/*
+ * Forget every level (keeps the traces and the memory); the next level to
+ * build is 1. Asynchronous on the context's stream. A context whose hash table
+ * has at least 2^23 slots builds its first levels in a small 8 MiB table and
+ * clears the large one meanwhile on a stream of its own (ordered after the
+ * work queued on the context's stream before this call); the level that first
+ * needs the large table waits for that clear, a solve that returns earlier
+ * joins it into the context's stream, and lsyn_destroy waits for it.
+ * Errors: LSYN_E_INVAL (NULL), LSYN_E_STATE (a batch or server problem),
+ * LSYN_E_CUDA.
+ */
 lsyn_status lsyn_reset(lsyn_ctx* ctx);
 
 /*

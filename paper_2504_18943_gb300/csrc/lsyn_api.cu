@@ -43,6 +43,17 @@ double lsyn::now_ms() {
 
 namespace {
 
+// Clears the large table beside the first levels after a reset: one block
+// per SM walking the table in grid strides, so that the level kernels on the
+// caller's stream still find room on every SM (a memset's grid holds the SMs
+// until it drains, and the first levels would wait behind it); streaming
+// stores keep the zeroed lines from evicting the levels' rows from L2.
+__global__ void __launch_bounds__(256) k_clear_table(uint4* t, size_t n16) {
+  const size_t stride = size_t(gridDim.x) * blockDim.x;
+  const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n16; i += stride) __stcs(t + i, z);
+}
+
 __global__ void k_level_begin(DevCounters* c) {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -513,8 +524,11 @@ void lsyn_destroy(lsyn_ctx* c) {
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
+  if (c->side) cudaStreamSynchronize(c->side);  // a clear of the big table may still run there
   if (c->events_ready)
     for (auto& e : c->ev) if (e) cudaEventDestroy(e);
+  for (auto& e : c->ev_side) if (e) cudaEventDestroy(e);
+  if (c->side) cudaStreamDestroy(c->side);
   c->mem.release_all();
   if (c->owns_host) {
     if (c->h_snap) cudaFreeHost(c->h_snap);
@@ -661,6 +675,18 @@ lsyn_status lsyn::ctx_create(const lsyn_problem* problem, const lsyn_config* con
   if (!c->arena || !c->prov || !c->table || !c->ctr || !c->consts || !c->atoms || !c->defer[0] || !c->defer[1] ||
       !c->fbuf || !c->fstatus || !c->slotpos || !c->homes || !c->holes || !c->moves || !c->hole_bits)
     return bail(LSYN_E_NOMEM, "device allocation failed");
+  c->big_table = c->table;
+  c->big_cap = c->table_cap;
+  if (c->big_cap >= 8 * lsyn_ctx::kFrontSlots) {
+    c->front_table = static_cast<unsigned long long*>(c->mem.get(size_t(lsyn_ctx::kFrontSlots) * 8));
+    if (!c->front_table) return bail(LSYN_E_NOMEM, "device allocation failed");
+    if ((e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking)) != cudaSuccess)
+      return bail(LSYN_E_CUDA, cudaGetErrorString(e));
+    for (auto& ev : c->ev_side)
+      if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+        return bail(LSYN_E_CUDA, cudaGetErrorString(e));
+    c->front_cap = lsyn_ctx::kFrontSlots;
+  }
   if (cudaMallocHost(&c->h_snap, sizeof(Snap) * lsyn_ctx::kSnaps) != cudaSuccess ||
       cudaMallocHost(&c->h_fbuf, lsyn_ctx::kFormulaCap) != cudaSuccess ||
       cudaMallocHost(&c->h_fstatus, sizeof(int)) != cudaSuccess) {
@@ -689,7 +715,31 @@ lsyn_status lsyn_reset(lsyn_ctx* c) {
   if (!c) return LSYN_E_INVAL;
   if (c->borrowed) return c->fail(LSYN_E_STATE, "a batch or server problem is driven by its owner");
   cudaSetDevice(c->device);
-  cudaError_t e = cudaMemsetAsync(c->table, 0, size_t(c->table_cap) * 8, c->stream);
+  cudaError_t e;
+  if (c->front_cap) {
+    // the front table now; the big one on the side stream, after the work
+    // queued so far on the main stream (which may still read it)
+    e = cudaMemsetAsync(c->front_table, 0, size_t(c->front_cap) * 8, c->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_side[0], c->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side, c->ev_side[0], 0);
+    // An SM runs blocks of kernels side by side only while its shared-memory
+    // carveout suits them all: the clear asks for the largest carveout, which
+    // every level and close kernel fits in, so that none waits for the clear.
+    static const cudaError_t carve = cudaFuncSetAttribute(
+        (const void*)k_clear_table, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess) e = carve;
+    if (e == cudaSuccess) {
+      k_clear_table<<<c->sms, 256, 0, c->side>>>(reinterpret_cast<uint4*>(c->big_table), size_t(c->big_cap) / 2);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_side[1], c->side);
+    c->table = c->front_table;
+    c->table_cap = c->front_cap;
+    c->front_active = true;
+    c->big_clear_pending = true;
+  } else {
+    e = cudaMemsetAsync(c->table, 0, size_t(c->table_cap) * 8, c->stream);
+  }
   if (e == cudaSuccess) e = cudaMemsetAsync(c->ctr, 0, sizeof(DevCounters), c->stream);
   if (e != cudaSuccess) return c->cuda_fail(e, "reset");
   c->level_start.assign(1, 0);
@@ -739,6 +789,26 @@ lsyn_status lsyn_enumerate_level(lsyn_ctx* c, int32_t k, lsyn_level_stats* out) 
   k_level_begin<<<1, 1, 0, c->stream>>>(c->ctr);
   ++launches;
   if ((e = cudaGetLastError()) != cudaSuccess) return c->cuda_fail(e, "level begin");
+  // Leave the front table before a level whose candidates could load it past
+  // table_load: wait for the big table's clear, then re-insert every entry's
+  // slot there (by its hash home; levels are closed, so every slot is
+  // published). An overflow of the rebuild is reported with the level.
+  if (c->front_active) {
+    const long long cand = level_candidate_count(c, k);  // negative: overflowed, so unbounded
+    if (cand < 0 || double(start) + double(cand) > double(c->front_cap) * c->table_load) {
+      if ((e = cudaStreamWaitEvent(c->stream, c->ev_side[1], 0)) != cudaSuccess) return c->cuda_fail(e, "table switch");
+      c->big_clear_pending = false;
+      e = c->word_bits == 32 ? Kernels<uint32_t>::rehash(c->front_table, c->front_cap, c->big_table, c->big_cap,
+                                                         c->homes, c->slotpos, start, &c->ctr->error, lc)
+                             : Kernels<uint64_t>::rehash(c->front_table, c->front_cap, c->big_table, c->big_cap,
+                                                         c->homes, c->slotpos, start, &c->ctr->error, lc);
+      ++launches;
+      if (e != cudaSuccess) return c->cuda_fail(e, "table switch");
+      c->table = c->big_table;
+      c->table_cap = c->big_cap;
+      c->front_active = false;
+    }
+  }
   ev_end(3);
 
   // Each launch counts into its own kind of the level's counters
@@ -923,6 +993,10 @@ lsyn_status lsyn_solve(lsyn_ctx* c, int32_t max_size, lsyn_result* out) {
   }
   c->solve_deadline_ms = 0;
   c->level_budget_ns = 0;
+  // a solve that ended on the front table: the big table's clear joins the
+  // caller's stream here, so that the solve's stream order covers it
+  if (c->big_clear_pending && cudaStreamWaitEvent(c->stream, c->ev_side[1], 0) == cudaSuccess)
+    c->big_clear_pending = false;
   out->levels_done = c->levels_done;
   out->constructed = int64_t(c->constructed);
   out->unique = int64_t(c->level_start.back() + c->level_n.back());

@@ -121,8 +121,22 @@ struct lsyn_ctx {
   // device memory
   uint4* arena = nullptr;
   unsigned long long* prov = nullptr;
-  unsigned long long* table = nullptr;
+  unsigned long long* table = nullptr;  // the table in use (the front table or the big one)
   unsigned long long table_cap = 0;
+  // The front table: after a reset the first levels use a small table
+  // (kFrontSlots slots, held in L2) while the big table, sized for the whole
+  // cache, is cleared on a side stream; before the first level whose
+  // candidates could load the front table past table_load the big table's
+  // clear is joined and the entries are re-inserted into it.
+  static constexpr unsigned long long kFrontSlots = 1ull << 20;
+  unsigned long long* big_table = nullptr;
+  unsigned long long big_cap = 0;
+  unsigned long long* front_table = nullptr;
+  unsigned long long front_cap = 0;  // 0: no front table (the big table is small)
+  bool front_active = false;         // `table` is the front table
+  bool big_clear_pending = false;    // the side stream's clear of the big table is not joined yet
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_side[2] = {};       // 0: the main stream reached the reset; 1: the big table is clear
   unsigned max_entries = 0;
   DevCounters* ctr = nullptr;
   uint4* consts = nullptr;  // [5][vecs]: lenmask, label, care, key, mul

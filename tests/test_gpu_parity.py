@@ -246,6 +246,57 @@ def test_mid_solve_full_size_each_tile(L, mid_oracle, tile):
 test_mid_solve_full_size_each_tile.sizes = {}
 
 
+def test_mid_levels_after_solve_and_reset(L, mid_oracle):
+    """One context solving the benchmark's problem again and again, as the
+    benchmark does. After a reset the first levels fill a small table while the
+    large one, left full by the previous solve, is cleared on a second stream;
+    level 8 (the first whose candidates could overfill the small table) moves
+    every entry into the large one. After a complete solve and a reset, levels
+    1..8 equal the oracle's as sets, and the next solve gives the same size."""
+    p, spec, levels, _ = mid_oracle
+    with L.Synthesizer(L.pack_problem(p), L.torch_config(cache_bytes=64 << 30)) as s:
+        st, res, f, _ = s.solve(16)
+        assert st == L.LSYN_OK and spec.separates(f)
+        size = res.size
+        s.reset()
+        for k in range(1, MID_FULL_DEPTH + 1):
+            st_k = s.level(k)
+            assert not st_k.cache_full and st_k.unique == levels[k].shape[0], (k, st_k.unique)
+            assert np.array_equal(sorted_rows(s.export(k)), levels[k]), f"level {k} differs after a reset"
+        for _ in range(2):
+            s.reset()
+            st, res, f, _ = s.solve(16)
+            assert st == L.LSYN_OK and res.size == size and spec.separates(f)
+
+
+@pytest.mark.parametrize("torch_alloc", [False, True])
+def test_small_table_reuse_tiny(L, torch_alloc):
+    """Tiny problems with a cache large enough for the two-table scheme (the
+    large table is cleared on a second stream after each reset while the
+    levels fill the small one, which these problems never leave): repeated
+    solves on one context give the oracle's minimal size, and after them the
+    complete levels equal the oracle's as sets."""
+    depth = 5
+    for seed in range(6):
+        p = W.tiny_problem(seed, oracle.labeller)
+        spec = oracle.Spec.from_problem(p)
+        size, _, _ = spec.solve(7)
+        mk = L.torch_config if torch_alloc else L.make_config
+        with L.Synthesizer(L.pack_problem(p), mk(cache_bytes=2 << 30, full_levels=True)) as s:
+            for _ in range(3):
+                s.reset()
+                st, res, f, _ = s.solve(7)
+                assert res.size == size, (seed, res.size, size)
+                if size:
+                    assert st == L.LSYN_OK and spec.separates(f)
+            s.reset()
+            ref = spec.enumerate(depth)
+            for k in range(1, depth + 1):
+                s.level(k)
+                got = sorted(L.cm_strings(row, p.traces.lengths) for row in s.export(k))
+                assert got == sorted(ref.cms(k)), (seed, k)
+
+
 def _edge(name, pos, neg, props, word_bits=32):
     return W.problem_from_strings(name, pos, neg, props, word_bits)
 
