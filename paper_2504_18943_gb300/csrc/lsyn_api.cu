@@ -915,9 +915,10 @@ lsyn_status lsyn_enumerate_level(lsyn_ctx* c, int32_t k, lsyn_level_stats* out) 
   }
   if (h.error) {
     static const char* const what[] = {"", "hash table probe overflow", "hole log overflow",
-                                       "hole fixup found an inconsistent slot", "inconsistent hole log"};
+                                       "hole fixup found an inconsistent slot", "inconsistent hole log",
+                                       "hash table rebuild overflow", "an operand row copy did not complete"};
     return c->fail(LSYN_E_STATE, std::string("internal consistency check failed: ") +
-                                     (h.error < 5 ? what[h.error] : "unknown code"));
+                                     (h.error < 7 ? what[h.error] : "unknown code"));
   }
   const uint32_t total = std::min(h.n_entries, c->max_entries);
   lsyn_status st = ctx_commit_level(c, k, c->h_snap[snap - 1].c, total, deferred, lp, out);

@@ -597,6 +597,47 @@ __device__ __forceinline__ void cp_async16(uint4* smem, const uint4* gmem) {
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// Bulk copies of whole rows into shared memory (the TMA unit's non-tensor
+// form), completed on a per-warp mbarrier: lane 0 arms the barrier with the
+// bytes to expect and issues the copies; every lane then waits on the
+// barrier's phase. Addresses are 16-byte aligned and sizes multiples of 16.
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0u;
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+// Orders this thread's earlier shared-memory accesses (and, after a warp
+// barrier, its warp's) before later accesses of the async proxy (bulk copies).
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Waits for phase `parity` of the barrier, at most `limit` polls per lane;
+// warp-uniform result (false: some lane gave up).
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity, unsigned limit) {
+  bool done = false;
+  for (unsigned i = 0; i < limit && !done; ++i) done = mbar_try_wait(bar, parity);
+  return __all_sync(0xFFFFFFFFu, done);
+}
+
 __device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
 __device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long long v) {
@@ -1230,7 +1271,7 @@ __global__ void __launch_bounds__(256, 3) k_desc_c(CacheView cv, const unsigned 
 // Operand rows are read through L1/L2 whenever a candidate is (re)computed;
 // compares read the stored row directly.
 // ===========================================================================
-template <typename W, int VPT = 1>
+template <typename W, int VPT = 1, int CU = 1>
 struct PathD {
   using Pending = WarpDedup::Pending;
   using Ids = WarpDedup::Ids;
@@ -1345,13 +1386,36 @@ struct PathD {
 #pragma unroll
         for (int o = 0; o < 4; ++o) src[o] = row_ptr(cv, __shfl_sync(kFull, cmp_id, 4 * g + o));  // published rows, read past L1
         uint32_t ne[4] = {0u, 0u, 0u, 0u};
-        for (unsigned r = 0; r < rv; ++r) {
-          const unsigned v = lane + 32u * r;
-          uint4 c[4];
-          gen.compute4(4 * g, v, c, sub);
+        if constexpr (CU == 1) {
+          for (unsigned r = 0; r < rv; ++r) {
+            const unsigned v = lane + 32u * r;
+            uint4 c[4];
+            gen.compute4(4 * g, v, c, sub);
 #pragma unroll
-          for (int o = 0; o < 4; ++o)
-            if ((sub >> o) & 1u) ne[o] |= v_ne(__ldcg(src[o] + v), c[o]);
+            for (int o = 0; o < 4; ++o)
+              if ((sub >> o) & 1u) ne[o] |= v_ne(__ldcg(src[o] + v), c[o]);
+          }
+        } else {
+        // CU vectors per lane of each stored row read together (their loads in
+        // flight at once), then compared
+        for (unsigned r = 0; r < rv; r += CU) {
+          uint4 st[CU][4];
+#pragma unroll
+          for (int u = 0; u < CU; ++u)
+#pragma unroll
+            for (int o = 0; o < 4; ++o)
+              st[u][o] = ((sub >> o) & 1u) && r + u < rv ? __ldcg(src[o] + lane + 32u * (r + u))
+                                                          : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+          for (int u = 0; u < CU; ++u) {
+            if (r + u >= rv) break;
+            uint4 c[4];
+            gen.compute4(4 * g, lane + 32u * (r + u), c, sub);
+#pragma unroll
+            for (int o = 0; o < 4; ++o)
+              if ((sub >> o) & 1u) ne[o] |= v_ne(st[u][o], c[o]);
+          }
+        }
         }
 #pragma unroll
         for (int o = 0; o < 4; ++o)
@@ -1546,6 +1610,92 @@ __global__ void __launch_bounds__(256) k_unary_d(CacheView cv, uint32_t first, u
     gen.id0 = first + base;
     const uint32_t en = en_ops & (nrows >= 8u ? 0xFFFFFFFFu : ((1u << (4 * nrows)) - 1u));
     P::template batch<false>(cv, gen, int(4 * nrows), en, pend, idr);
+    built += __popc(en);
+  }
+  WarpDedup::flush(pend);
+  WarpDedup::retire(cv, idr);
+  if (lane == 0 && built) atomicAdd(&cv.ctr->built_k[cv.kind], built);
+}
+
+// Staged form of k_unary_d for one-plane CMs of 8-16 KiB. Each warp copies
+// its operand row into shared memory with one bulk copy (the TMA unit moves the
+// whole row while the warp waits on an mbarrier) and every pass of the batch
+// (hash and specification check, in-batch twins, compares, writes) computes
+// the four operators from that copy: the row is read from HBM once, where
+// k_unary_d reads it again after its probes and, with 16 KiB rows, finds it
+// evicted from L2 about a quarter of the time. Shared memory bounds the block
+// to as many warps as rows of M bytes fit its shared memory: 14 with 16 KiB
+// rows.
+constexpr unsigned kStagedMinBytes = 8192, kStagedMaxBytes = 16384;
+constexpr int kStagedMaxWarps = 16;
+constexpr unsigned kBulkChunk = 4096;        // bytes per bulk copy instruction
+constexpr unsigned kRowWaitPolls = 1u << 22; // polls of the row's barrier before the warp gives up
+// Vectors per lane of each stored row that the compare pass of k_unary_ds
+// loads together: with few warps per SM, a compare read one vector at a time
+// was a chain of 32 round trips per 16 KiB row.
+constexpr int kCmpVecsDS = 4;
+
+template <typename W>
+struct RowGenDS {
+  const CacheView* cv;
+  const uint4* row;  // shared memory: the operand row
+  uint32_t id0;
+  __device__ uint4 compute(int q, unsigned v) const {
+    const uint4 x = row[v];
+    return v_op<W>(unary_code(q & 3), x, x, __ldg(cv->lenmask + v), 0);
+  }
+  __device__ void compute4(int /*q0*/, unsigned v, uint4 (&c)[4], uint32_t /*sub*/ = 0xFu) const {
+    const uint4 x = row[v], lm = __ldg(cv->lenmask + v);
+#pragma unroll
+    for (int o = 0; o < 4; ++o) c[o] = v_op<W>(unary_code(o), x, x, lm, 0);
+  }
+  __device__ uint64_t desc(int q) const { return pack_desc(unary_code(q & 3), id0, 0); }
+};
+
+template <typename W>
+__global__ void __launch_bounds__(32 * kStagedMaxWarps) k_unary_ds(CacheView cv, uint32_t first, uint32_t count,
+                                                                   uint32_t ops) {
+  using P = PathD<W, kVptUnaryD, kCmpVecsDS>;
+  extern __shared__ __align__(128) uint4 smem_rows[];
+  __shared__ unsigned long long s_bar[kStagedMaxWarps];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const unsigned row_bytes = cv.vecs * 16u;
+  uint4* row = smem_rows + size_t(wib) * cv.vecs;
+  unsigned long long* bar = s_bar + wib;
+  if (lane == 0) mbar_init(bar, 1u);
+  __syncwarp();
+  RowGenDS<W> gen;
+  gen.cv = &cv;
+  gen.row = row;
+  const uint32_t en = ops & 0xFu;  // the four operators of the row, as enabled
+  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  unsigned long long built = 0;
+  typename P::Pending pend;
+  typename P::Ids idr;
+  unsigned parity = 0;
+  for (uint32_t base = warp; base < count; base += nwarps) {
+    if (__any_sync(kFull, stop_requested(cv))) break;
+    // every lane's reads of the previous row are done before the copy overwrites it
+    __syncwarp();
+    if (lane == 0) {
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(bar, row_bytes);
+      const char* src = reinterpret_cast<const char*>(row_ptr(cv, first + base));
+      char* dst = reinterpret_cast<char*>(row);
+      for (unsigned off = 0; off < row_bytes; off += kBulkChunk)
+        bulk_load(dst + off, src + off, min(kBulkChunk, row_bytes - off), bar);
+    }
+    if (!mbar_wait_bounded(bar, parity, kRowWaitPolls)) {
+      // cannot happen while the copy engine works: record it, give the copy a
+      // second bounded wait (it writes this block's shared memory) and stop
+      if (lane == 0) atomicExch(&cv.ctr->error, 6u);
+      mbar_wait_bounded(bar, parity, kRowWaitPolls);
+      break;
+    }
+    parity ^= 1u;
+    gen.id0 = first + base;
+    P::template batch<false>(cv, gen, 4, en, pend, idr);
     built += __popc(en);
   }
   WarpDedup::flush(pend);
@@ -2178,7 +2328,7 @@ static __global__ void __launch_bounds__(256) k_rehash(const unsigned long long*
     for (; it <= new_mask; ++it, pos = (pos + 1) & new_mask)
       if (atomicCAS(new_t + pos, 0ull, v) == 0ull) break;
     if (it > new_mask) {
-      atomicExch(error, 4u);
+      atomicExch(error, 5u);
       continue;
     }
     slotpos[id] = unsigned(pos);
@@ -2392,6 +2542,27 @@ struct LaunchD {
     return cudaGetLastError();
   }
   static cudaError_t unary(const CacheView& cv, uint32_t first, uint32_t count, uint32_t ops, const LaunchCfg& lc) {
+    const unsigned M = cv.vecs * 16u;
+    if (cv.planes <= 1 && M >= kStagedMinBytes && M <= kStagedMaxBytes) {
+      // one block per SM holding as many warps as rows fit its shared memory
+      static int optin = [] {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+          v = 0;
+        return v;
+      }();
+      const int dyn_cap = optin - 1024;  // room for the kernel's static shared memory
+      const unsigned warps = dyn_cap > 0 ? std::min(unsigned(kStagedMaxWarps), unsigned(dyn_cap) / M) : 0u;
+      if (warps >= 4u) {
+        static const cudaError_t attr = cudaFuncSetAttribute((const void*)k_unary_ds<W>,
+                                                             cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_cap);
+        if (attr != cudaSuccess) return attr;
+        const unsigned blocks = std::max(1u, std::min((count + warps - 1u) / warps, unsigned(lc.sms)));
+        k_unary_ds<W><<<blocks, 32u * warps, size_t(warps) * M, lc.stream>>>(cv, first, count, ops);
+        return cudaGetLastError();
+      }
+    }
     static int occ = occupancy_blocks((const void*)k_unary_d<W>, 256, 0);
     const unsigned blocks = std::max(1u, std::min((count + 63u) / 64u, unsigned(lc.sms * occ)));
     k_unary_d<W><<<blocks, 256, 0, lc.stream>>>(cv, first, count, ops);

@@ -427,6 +427,17 @@ def test_matrices_above_64k_unsupported(L):
     assert ei.value.status == L.LSYN_E_UNSUPPORTED
 
 
+@pytest.mark.parametrize("word_bits,n_traces", [(64, 1000), (32, 2900), (64, 2000)])
+def test_levels_staged_unary_rows(L, word_bits, n_traces):
+    """CMs of 8, 11.5 and 16 KiB in one plane, where the unary launch copies
+    each operand row into shared memory with one bulk copy and computes every
+    pass of its batch from that copy: levels 1..5 equal the oracle's as sets."""
+    half = n_traces // 2
+    p = W.labelled_problem("staged", 11 + n_traces, 3, half, n_traces - half, 4, min(word_bits, 24), 5, word_bits,
+                           oracle.labeller)
+    assert_levels_match(L, p, 5, cache_bytes=4 << 30)
+
+
 def test_large_workload_full_size(L):
     """The large configuration at its stated size (10 propositions, 1024 +
     1024 traces of length 16..64, 16 KiB CMs, a 150 GB cache), levels built
