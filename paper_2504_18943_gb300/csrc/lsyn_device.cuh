@@ -697,11 +697,16 @@ struct WarpDedup {
   __device__ static unsigned take(const Ids& ids, unsigned n_claim, unsigned have, unsigned base, bool use_pre) {
     return n_claim > have ? __shfl_sync(kFull, use_pre ? ids.pre : base, 0) : 0u;
   }
+  // Ids reserved on demand for a batch that needs n_claim - have more: a full
+  // chunk, or exactly those in a warp's last batch (nothing is left to hole).
+  __device__ static unsigned demand(const CacheView& cv, unsigned n_claim, unsigned have, bool last) {
+    return last ? n_claim - have : max(cv.chunk, n_claim - have);
+  }
   __device__ static void advance(const CacheView& cv, Ids& ids, unsigned n_claim, unsigned have, unsigned fresh,
-                                 bool use_pre) {
+                                 bool use_pre, bool last = false) {
     if (n_claim > have) {
       ids.next = fresh + (n_claim - have);
-      ids.end = fresh + (use_pre ? cv.chunk : max(cv.chunk, n_claim - have));
+      ids.end = fresh + (use_pre ? cv.chunk : demand(cv, n_claim, have, last));
       if (use_pre) ids.pre_ok = false;
     } else {
       ids.next += n_claim;
@@ -802,11 +807,14 @@ struct PathC {
   // generators whose consecutive batches share an operand, so that a warp never
   // defers on its own inserts); otherwise after probing, when the fence no
   // longer waits for those stores.
+  // last (warp-uniform): the warp's final batch of the launch; it reserves no
+  // chunk ahead and takes exactly the ids its inserts need, so that its
+  // unused ids (holes, moved at the level's close) stay few.
   template <bool kEarlyPublish, class Gen>
   __device__ static void batch(const CacheView& cv, const Consts& k, const Gen& gen, int n, uint32_t en,
-                               uint4* stage, Pending& pend, Ids& ids) {
+                               uint4* stage, Pending& pend, Ids& ids, bool last = false) {
     const int lane = threadIdx.x & 31;
-    WarpDedup::prefetch(cv, ids);
+    if (!last) WarpDedup::prefetch(cv, ids);
     uint32_t my_lo = 0, my_hi = 0, bad = 0;
     for (int q0 = 0; q0 < n; q0 += 4) {  // n is a multiple of 4: four operators per operand group
       uint4 c4[4];
@@ -915,7 +923,7 @@ struct PathC {
     const bool use_pre = n_claim > have && ids.pre_ok;
     unsigned base = 0;
     if (n_claim > have && !use_pre && lane == 0)
-      base = atomicAdd(&cv.ctr->n_entries, max(cv.chunk, n_claim - have));
+      base = atomicAdd(&cv.ctr->n_entries, WarpDedup::demand(cv, n_claim, have, last));
     if (!kEarlyPublish) WarpDedup::flush(pend);  // overlaps the id reservation above
     if (claim) {
       const unsigned fresh = WarpDedup::take(ids, n_claim, have, base, use_pre);
@@ -927,7 +935,7 @@ struct PathC {
       }
       const unsigned my_rank = unsigned(__popc(claim & ((1u << lane) - 1u)));
       const unsigned my_id = my_rank < have ? ids.next + my_rank : fresh + (my_rank - have);
-      WarpDedup::advance(cv, ids, n_claim, have, fresh, use_pre);
+      WarpDedup::advance(cv, ids, n_claim, have, fresh, use_pre, last);
       ids.inserted += __popc(__ballot_sync(kFull, state == kClaimed && my_id < cv.max_entries));
       if (state == kClaimed) {
         unsigned long long* slot = cv.table + pos;
@@ -1067,7 +1075,8 @@ __global__ void __launch_bounds__(256, 3) k_unary_c(CacheView cv, uint32_t first
     __syncwarp();
     gen.id0 = first + base;
     const uint32_t en = en_ops & ((nrows >= 8u ? 0xFFFFFFFFu : ((1u << (4 * nrows)) - 1u)));
-    P::template batch<false>(cv, k, gen, int(4 * nrows), en, stage, pend, idr);
+    const bool last = base + nwarps * ROWS >= count;
+    P::template batch<false>(cv, k, gen, int(4 * nrows), en, stage, pend, idr, last);
     built += __popc(en);
     __syncwarp();
   }
@@ -1205,10 +1214,11 @@ __global__ void __launch_bounds__(256, 3) k_binary_small_c(CacheView cv, BinaryP
     __syncwarp();
     gen.a0 = S.left_start + l0;
     const uint32_t en = en_ops & (np >= 8u ? 0xFFFFFFFFu : ((1u << (4 * np)) - 1u));
+    const bool last_item = c + nwarps >= plan.total_tiles;
     for (uint32_t r = r0; r < r1; ++r) {
       gen.b_id = S.right_start + r;
       gen.b = __ldg(row_ptr(cv, gen.b_id) + lane);
-      P::template batch<true>(cv, k, gen, int(4 * np), en, stage, pend, idr);
+      P::template batch<true>(cv, k, gen, int(4 * np), en, stage, pend, idr, last_item && r + 1u == r1);
       built += __popc(en);
     }
     __syncwarp();
