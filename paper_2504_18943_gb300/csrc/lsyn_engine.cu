@@ -1075,10 +1075,17 @@ lsyn_status Engine::lane_launch(Lane& L, Job* j, bool* progressed) {
   for (const Job* x : active_) light = light || (!x->heavy && x != j);
   const LaunchCfg lc{L.stream, light ? sms_ - light_sms() : sms_};
   const CacheView cv = c->view(c->defer[0], &c->ctr->defer_n[0]);
+  // CMs above 512 bytes (path D): the unary launch and the deferred passes
+  // reserve exactly each batch's ids, as on the one-problem path. Ids a warp
+  // leaves unused count against the job's entries until the level closes, so
+  // chunks held by many warps (a deferred pass spreads a short list over many
+  // warps) could fill a cache at its cap that the one-problem path fits.
+  CacheView uv = cv;
+  if (c->vecs > 32u) uv.chunk = 1;
   cudaError_t e = launch_level_begin(c->ctr, L.stream);
   if (e == cudaSuccess && L.lp.uops && L.lp.u_count)
-    e = c->word_bits == 32 ? Kernels<uint32_t>::unary(cv, L.lp.u_first, L.lp.u_count, L.lp.uops, lc)
-                           : Kernels<uint64_t>::unary(cv, L.lp.u_first, L.lp.u_count, L.lp.uops, lc);
+    e = c->word_bits == 32 ? Kernels<uint32_t>::unary(uv, L.lp.u_first, L.lp.u_count, L.lp.uops, lc)
+                           : Kernels<uint64_t>::unary(uv, L.lp.u_first, L.lp.u_count, L.lp.uops, lc);
   if (e == cudaSuccess && L.lp.plan.n_splits > 0)
     e = c->word_bits == 32 ? Kernels<uint32_t>::binary(cv, L.lp.plan, lc)
                            : Kernels<uint64_t>::binary(cv, L.lp.plan, lc);
@@ -1090,6 +1097,7 @@ lsyn_status Engine::lane_launch(Lane& L, Job* j, bool* progressed) {
   if (e == cudaSuccess) {
     CacheView rv = c->view(c->defer[1], &c->ctr->defer_n[1]);
     rv.early_exit = 0;  // a deferred candidate must be settled even after a solution
+    if (c->vecs > 32u) rv.chunk = 1;
     e = c->word_bits == 32 ? Kernels<uint32_t>::desc_list(rv, c->defer[0], &c->ctr->defer_n[0], c->defer_cap, 0, lc)
                            : Kernels<uint64_t>::desc_list(rv, c->defer[0], &c->ctr->defer_n[0], c->defer_cap, 0, lc);
   }
@@ -1214,6 +1222,7 @@ lsyn_status Engine::lane_advance(Lane& L, bool* progressed) {
         e = cudaMemsetAsync(&c->ctr->defer_n[1 - cur], 0, sizeof(unsigned), L.stream);
         CacheView rv = c->view(c->defer[1 - cur], &c->ctr->defer_n[1 - cur]);
         rv.early_exit = 0;  // a deferred candidate must be settled even after a solution
+        if (c->vecs > 32u) rv.chunk = 1;  // as the level's first pass
         if (e == cudaSuccess)
           e = c->word_bits == 32 ? Kernels<uint32_t>::desc_list(rv, c->defer[cur], &c->ctr->defer_n[cur], nd, 0, lc)
                                  : Kernels<uint64_t>::desc_list(rv, c->defer[cur], &c->ctr->defer_n[cur], nd, 0, lc);

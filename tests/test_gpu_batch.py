@@ -47,6 +47,30 @@ def test_batch_equals_plain_path(L, problems):
     assert any(s == L.LSYN_OK for s in statuses)
 
 
+def test_full_batch_answers_equal_plain_path(L):
+    """The 256-problem batch at its benchmark settings (8 GiB cap per problem,
+    sizes up to 13; a few problems fill their cap, several need gigabytes):
+    every problem's status and size equal the one-problem path's. Ids that
+    warps reserve and leave unused count against a cache until its level
+    closes, so the scheduler's path-D unary launches and deferred passes
+    reserve exactly each batch's ids, as the one-problem path does; with
+    per-warp chunks, three of these problems filled their cap one level before
+    the answer the one-problem path finds."""
+    import torch
+    packed = [L.pack_problem(W.batched_problem(1000, i, L.labeller)) for i in range(256)]
+    with L.Batch(packed, L.make_config(cache_bytes=8 << 30)) as b:
+        statuses, results, formulas = b.solve(13)
+    assert statuses.count(L.LSYN_OK) > 200
+    torch.cuda.empty_cache()
+    cfg = L.torch_config(cache_bytes=8 << 30)
+    for i, q in enumerate(packed):
+        with L.Synthesizer(q, cfg) as s:
+            st, res, f, _ = s.solve(13)
+        assert statuses[i] == st, (i, statuses[i], st)
+        if st == L.LSYN_OK:
+            assert results[i].size == res.size, (i, results[i].size, res.size)
+
+
 def test_batch_levels_equal_oracle(L, problems):
     small = [p for p in problems if p.n_traces <= 120][:4]
     packed = [L.pack_problem(p) for p in small]
