@@ -120,6 +120,11 @@ typedef void (*lsyn_free_fn)(void* ptr, void* user);
  *                allocator); NULL = cudaMalloc / cudaFree.
  *   stream       cudaStream_t for all device work; NULL = the legacy default stream.
  *   device       CUDA device ordinal; -1 or 0..n-1 (the current device if -1).
+ *                One process drives one device: the kernels' shared-memory
+ *                attributes are set once per process, on the device that
+ *                first launches them, so contexts, batches or servers of one
+ *                process on a second device fail their launches (LSYN_E_CUDA).
+ *                Run one process per GPU (as bench.py does).
  *   tile_rows    0: automatic; 8, 16 or 32: rows of each side of the block
  *                tiles of the binary launch for 512-byte CMs (k_binary_c),
  *                kept at every level. By default a tile starts at 32 rows and
