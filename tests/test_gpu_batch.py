@@ -58,6 +58,10 @@ def test_full_batch_answers_equal_plain_path(L):
     the answer the one-problem path finds."""
     import torch
     packed = [L.pack_problem(W.batched_problem(1000, i, L.labeller)) for i in range(256)]
+    # the scheduler's pool takes most of the free device memory, as in the
+    # benchmark: nothing cached by earlier tests may shrink it
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
     with L.Batch(packed, L.make_config(cache_bytes=8 << 30)) as b:
         statuses, results, formulas = b.solve(13)
     assert statuses.count(L.LSYN_OK) > 200
